@@ -1,0 +1,318 @@
+"""Python side of the CPU oracle.  TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
+(``cpu_baseline`` and ``--impl reference``) may import this module.  It shares
+no code with the CUDA library and never imports it.
+
+Contents (each function cites the passage it follows):
+  * ctypes wrappers around ``oracle.c`` (McMurchie-Davidson ERIs, J/K, gradient);
+  * J/K and the energy functional written as literal sums over a full AO
+    tensor (Eq. jkbuild, Eq. jkderiv);
+  * the least-squares Laplace quadrature (Eq. laplace), step by step;
+  * Laplace pseudo-densities (Eqs. scaledcoeff, aodens/aodensk with R = X);
+  * the brute-force energy-denominator sums that the quadrature must reproduce
+    (Eq. factorize).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (OpenMP) into oracle/_build/liboracle.so."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Basis(ctypes.Structure):
+    _fields_ = [("natoms", ctypes.c_int), ("coords", ctypes.c_void_p),
+                ("nshells", ctypes.c_int), ("sh_atom", ctypes.c_void_p),
+                ("sh_l", ctypes.c_void_p), ("sh_nprim", ctypes.c_void_p),
+                ("exps", ctypes.c_void_p), ("coefs", ctypes.c_void_p)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        D = ctypes.c_double
+        _lib.orc_boys.argtypes = [I, D, P]
+        _lib.orc_eri_prim.argtypes = [I, I, I, I, D, D, D, D, P, P, P, P, P]
+        _lib.orc_norm_coefs.argtypes = [I, P, P, P, P, P]
+        _lib.orc_shell_quartet.argtypes = [P, I, I, I, I, P]
+        _lib.orc_eri_tensor.argtypes = [P, P]
+        _lib.orc_schwarz.argtypes = [P, P]
+        _lib.orc_jk.argtypes = [P, I, P, D, P, P]
+        _lib.orc_j_block.argtypes = [P, I, P, D, I, I, P]
+        _lib.orc_k_block.argtypes = [P, I, P, D, I, I, P]
+        _lib.orc_grad.argtypes = [P, I, P, P, D, D, I, P]
+        _lib.orc_num_threads.restype = I
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class _BasisRef:
+    """Keeps the numpy arrays alive while the C struct points at them."""
+
+    def __init__(self, mol):
+        self.arrs = [np.ascontiguousarray(mol.coords, dtype=np.float64),
+                     np.ascontiguousarray(mol.shell_atom, dtype=np.int32),
+                     np.ascontiguousarray(mol.shell_l, dtype=np.int32),
+                     np.ascontiguousarray(mol.shell_nprim, dtype=np.int32),
+                     np.ascontiguousarray(mol.exps, dtype=np.float64),
+                     np.ascontiguousarray(mol.coefs, dtype=np.float64)]
+        c, a, l, n, e, k = self.arrs
+        self.s = _Basis(c.shape[0], c.ctypes.data, l.shape[0], a.ctypes.data, l.ctypes.data,
+                        n.ctypes.data, e.ctypes.data, k.ctypes.data)
+
+    @property
+    def p(self):
+        return ctypes.byref(self.s)
+
+
+def ncart(l):
+    return (l + 1) * (l + 2) // 2
+
+
+def nao(mol) -> int:
+    return int(sum(ncart(int(l)) for l in mol.shell_l))
+
+
+def shell_offsets(mol):
+    off = np.zeros(mol.nshells + 1, dtype=np.int64)
+    for s, l in enumerate(mol.shell_l):
+        off[s + 1] = off[s] + ncart(int(l))
+    return off
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+# ------------------------------------------------------------------ wrappers
+def boys(mmax: int, T: float) -> np.ndarray:
+    out = np.zeros(mmax + 1)
+    lib().orc_boys(mmax, float(T), _ptr(out))
+    return out
+
+
+def eri_prim(ls, es, centers) -> np.ndarray:
+    """Primitive block over unnormalised Cartesian Gaussians, shape [na, nb, nc, nd]."""
+    la, lb, lc, ld = ls
+    out = np.zeros(ncart(la) * ncart(lb) * ncart(lc) * ncart(ld))
+    cs = [np.ascontiguousarray(c, dtype=np.float64) for c in centers]
+    lib().orc_eri_prim(la, lb, lc, ld, *[float(e) for e in es], *[_ptr(c) for c in cs], _ptr(out))
+    return out.reshape(ncart(la), ncart(lb), ncart(lc), ncart(ld))
+
+
+def norm_coefs(mol) -> np.ndarray:
+    out = np.zeros_like(mol.exps)
+    lib().orc_norm_coefs(mol.nshells, _ptr(np.ascontiguousarray(mol.shell_l, dtype=np.int32)),
+                         _ptr(np.ascontiguousarray(mol.shell_nprim, dtype=np.int32)),
+                         _ptr(mol.exps), _ptr(mol.coefs), _ptr(out))
+    return out
+
+
+def shell_quartet(mol, a, b, c, d) -> np.ndarray:
+    ls = [int(mol.shell_l[s]) for s in (a, b, c, d)]
+    out = np.zeros(int(np.prod([ncart(l) for l in ls])))
+    br = _BasisRef(mol)
+    lib().orc_shell_quartet(br.p, a, b, c, d, _ptr(out))
+    return out.reshape([ncart(l) for l in ls])
+
+
+def eri_tensor(mol) -> np.ndarray:
+    """Full (mu nu|ka rho) tensor, every ordered shell quartet evaluated directly."""
+    N = nao(mol)
+    out = np.zeros(N ** 4)
+    br = _BasisRef(mol)
+    lib().orc_eri_tensor(br.p, _ptr(out))
+    return out.reshape(N, N, N, N)
+
+
+def schwarz(mol) -> np.ndarray:
+    """Q[a, b] = max sqrt|(mu nu|mu nu)| over mu in shell a, nu in shell b."""
+    ns = mol.nshells
+    out = np.zeros(ns * ns)
+    br = _BasisRef(mol)
+    lib().orc_schwarz(br.p, _ptr(out))
+    return out.reshape(ns, ns)
+
+
+def jk(mol, D: np.ndarray, tau: float = 0.0):
+    """J[D], K[D] for D [nd, N, N] by the canonical-integral loop with explicit
+    permutation images (Eq. jkbuild); Schwarz rule: skip iff Q_ab Q_cd < tau."""
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    nd, N, _ = D.shape
+    J = np.zeros_like(D)
+    K = np.zeros_like(D)
+    br = _BasisRef(mol)
+    lib().orc_jk(br.p, nd, _ptr(D), float(tau), _ptr(J), _ptr(K))
+    return J, K
+
+
+def j_block(mol, D, sa, sb, tau=0.0):
+    """J[q][mu][nu] for mu in shell sa, nu in shell sb, from the definition."""
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    nd = D.shape[0]
+    na, nb = ncart(int(mol.shell_l[sa])), ncart(int(mol.shell_l[sb]))
+    out = np.zeros(nd * na * nb)
+    br = _BasisRef(mol)
+    lib().orc_j_block(br.p, nd, _ptr(D), float(tau), sa, sb, _ptr(out))
+    return out.reshape(nd, na, nb)
+
+
+def k_block(mol, D, sa, sc, tau=0.0):
+    """K[q][mu][nu] for mu in shell sa, nu in shell sc, from the definition."""
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    nd = D.shape[0]
+    na, nc = ncart(int(mol.shell_l[sa])), ncart(int(mol.shell_l[sc]))
+    out = np.zeros(nd * na * nc)
+    br = _BasisRef(mol)
+    lib().orc_k_block(br.p, nd, _ptr(D), float(tau), sa, sc, _ptr(out))
+    return out.reshape(nd, na, nc)
+
+
+def grad(mol, P, Q, cJ, cK, atom_filter: int = -1) -> np.ndarray:
+    """d/dR sum_r [cJ J(P_r,Q_r) + cK K(P_r,Q_r)] (Eq. jkderiv), shape [natoms, 3]."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    out = np.zeros(mol.natoms * 3)
+    br = _BasisRef(mol)
+    lib().orc_grad(br.p, P.shape[0], _ptr(P), _ptr(Q), float(cJ), float(cK), int(atom_filter),
+                   _ptr(out))
+    return out.reshape(mol.natoms, 3)
+
+
+# -------------------------------------------------- literal sums over a tensor
+def jk_from_tensor(I: np.ndarray, D: np.ndarray):
+    """Eq. jkbuild written out: J_mn = sum_kr (mn|kr) D_kr, K_mn = sum_kr (mk|nr) D_kr."""
+    J = np.einsum("mnkr,qkr->qmn", I, D, optimize=True)
+    K = np.einsum("mknr,qkr->qmn", I, D, optimize=True)
+    return J, K
+
+
+def energy_from_tensor(I, P, Q, cJ, cK) -> float:
+    """E = sum_r [cJ J(P_r,Q_r) + cK K(P_r,Q_r)], with
+    J(A,B) = sum (mn|kr) A_mn B_kr and K(A,B) = sum (mk|nr) A_mn B_kr (Eq. jkderiv)."""
+    eJ = np.einsum("mnkr,qmn,qkr->", I, P, Q, optimize=True)
+    eK = np.einsum("mknr,qmn,qkr->", I, P, Q, optimize=True)
+    return float(cJ * eJ + cK * eK)
+
+
+# ----------------------------------------------------------- Laplace (Eq. laplace)
+def laplace_range(eps_occ, eps_vir):
+    """Fit range [2*gap, 2*span] of the doubles denominator D = e_a + e_b - e_i - e_j."""
+    return 2.0 * (np.min(eps_vir) - np.max(eps_occ)), 2.0 * (np.max(eps_vir) - np.min(eps_occ))
+
+
+def laplace_quadrature(xmin: float, xmax: float, n: int, nsample: int = 2000,
+                       ncheck: int = 100000, return_all: bool = False):
+    """Least-squares exponential sum sum_q w_q exp(-t_q x) ~ 1/x on [xmin, xmax] (Eq. laplace).
+
+    The paper asks for a short exponential-sum grid over the denominator range;
+    this oracle fits it in the least-squares sense:
+      (1) the problem is scale invariant, so fit on [1, R], R = xmax/xmin, and
+          map back with t -> t/xmin, w -> w/xmin;
+      (2) nsample log-spaced sample points x_s in [1, R];
+      (3) continuation in the number of points: a one-point fit, then for
+          k = 2..n one node is appended beyond the largest exponent (geometric
+          extrapolation) and all 2k parameters (log t, log w) are refined by
+          Levenberg-Marquardt (MINPACK, via scipy) on the relative residual
+          r_s = 1 - x_s sum_q w_q exp(-t_q x_s);
+      (4) the maximum relative error |x sum w exp(-t x) - 1| on ncheck
+          log-spaced points of [xmin, xmax].
+    Returns (t, w, max_rel_err), t ascending; with return_all, a dict k -> that triple."""
+    from scipy.optimize import least_squares
+
+    R = xmax / xmin
+    xs = np.geomspace(1.0, R, nsample)
+
+    def res(th, k):
+        with np.errstate(over="ignore", invalid="ignore"):
+            t, w = np.exp(th[:k]), np.exp(th[k:])
+            r = 1.0 - xs * (np.exp(-np.outer(xs, t)) @ w)
+        return np.where(np.isfinite(r), r, 1e150)
+
+    def jac(th, k):
+        with np.errstate(over="ignore", invalid="ignore"):
+            t, w = np.exp(th[:k]), np.exp(th[k:])
+            E = np.exp(-np.outer(xs, t))
+            Jm = np.concatenate([(xs ** 2)[:, None] * (w * t)[None, :] * E,
+                                 -xs[:, None] * w[None, :] * E], axis=1)
+        return np.where(np.isfinite(Jm), Jm, 0.0)
+
+    th = np.array([np.log(1.0 / np.sqrt(R)), 0.0])
+    out = {}
+    for k in range(1, n + 1):
+        if k > 1:
+            t, w = np.exp(th[:k - 1]), np.exp(th[k - 1:])
+            ratio = t[-1] / t[-2] if k > 2 else 3.0
+            t = np.append(t, t[-1] * ratio)
+            w = np.append(w, 0.5 * w[-1])
+            th = np.concatenate([np.log(t), np.log(w)])
+        th = least_squares(res, th, jac=jac, args=(k,), method="lm", xtol=1e-15, ftol=1e-15,
+                           gtol=1e-15, max_nfev=4000 * k).x
+        order = np.argsort(th[:k])
+        th = np.concatenate([th[:k][order], th[k:][order]])
+        if return_all or k == n:
+            t, w = np.exp(th[:k]) / xmin, np.exp(th[k:]) / xmin
+            out[k] = (t, w, laplace_error(t, w, xmin, xmax, ncheck))
+    return out if return_all else out[n]
+
+
+def laplace_error(t, w, xmin, xmax, ncheck=100000) -> float:
+    """max over a log-spaced grid of |x sum_q w_q exp(-t_q x) - 1|."""
+    xc = np.geomspace(xmin, xmax, ncheck)
+    return float(np.max(np.abs(xc * (np.exp(-np.outer(xc, t)) @ w) - 1.0)))
+
+
+# ---------------------------------------- pseudo-densities (Eqs. scaledcoeff, aodensk)
+def pseudo_densities(C_occ, C_vir, eps_occ, eps_vir, X, t) -> np.ndarray:
+    """D[q*npair + p] = U_q X_p V_q^T with U_q = C_o diag(e^{t_q eps_o}) and
+    V_q = C_v diag(e^{-t_q eps_v}) (Eq. scaledcoeff; Eq. aodensk with the residual
+    replaced by the amplitudes X_p).  No quadrature weight is folded in."""
+    nlap, npair = len(t), X.shape[0]
+    N = C_occ.shape[0]
+    D = np.zeros((nlap * npair, N, N))
+    for q in range(nlap):
+        U = C_occ * np.exp(t[q] * eps_occ)[None, :]
+        V = C_vir * np.exp(-t[q] * eps_vir)[None, :]
+        for p in range(npair):
+            D[q * npair + p] = U @ X[p] @ V.T
+    return D
+
+
+def denominator_sums(I, C_occ, C_vir, eps_occ, eps_vir, X):
+    """Brute-force sums the quadrature must reproduce (Eq. factorize):
+    SJ = sum_{ia,jb} X_ia X_jb (ia|jb) / (d_ia + d_jb),
+    SK = sum_{ia,jb} X_ia X_jb (ij|ab) / (d_ia + d_jb), d_ia = e_a - e_i,
+    and the matching sums of absolute values (for the error bound)."""
+    ovov = np.einsum("mi,na,kj,rb,mnkr->iajb", C_occ, C_vir, C_occ, C_vir, I, optimize=True)
+    oovv = np.einsum("mi,nj,ka,rb,mnkr->ijab", C_occ, C_occ, C_vir, C_vir, I, optimize=True)
+    d = eps_vir[None, :] - eps_occ[:, None]
+    den = d[:, :, None, None] + d[None, None, :, :]
+    XX = np.einsum("ia,jb->iajb", X, X)
+    tJ = XX * ovov / den
+    tK = XX * oovv.transpose(0, 2, 1, 3) / den
+    return float(tJ.sum()), float(tK.sum()), float(np.abs(tJ).sum()), float(np.abs(tK).sum())
