@@ -1,0 +1,190 @@
+/*
+ * ltjk.h -- C ABI of the GB300 Laplace-transform AO-direct J/K library.
+ *
+ * The library computes, on one GPU, the Coulomb and exchange builds of many
+ * non-symmetric AO densities with electron-repulsion integrals evaluated on the
+ * fly over Schwarz-screened Cartesian Gaussian shell quartets, the Laplace
+ * pseudo-densities that feed them, and the nuclear-gradient adjoint of the
+ * build.  Equations are cited by the paper's labels (arXiv 2607.05622).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: LTJK_OK (0) or a negative code
+ *     below.  On failure ltjk_last_error() (thread-local) describes the cause
+ *     and no output is guaranteed to be written.
+ *   - Arrays are DEVICE pointers unless the argument name ends in _host.  The
+ *     caller owns every array; the library never frees caller memory.
+ *   - Matrices are row-major FP64.  A stack of n AO matrices is [n][N][N] with
+ *     N = number of Cartesian AOs; element (q, mu, nu) sits at q*N*N + mu*N + nu.
+ *   - AO order: shells in input order; within a shell of angular momentum l the
+ *     Cartesian components x^lx y^ly z^lz ordered by descending lx, then
+ *     descending ly.  A contracted shell is sum_k c_k N_k g_k with g_k the
+ *     primitive of exponent a_k, N_k = (2a_k/pi)^{3/4} (4a_k)^{l/2} / sqrt((2l-1)!!)
+ *     (unit norm for the x^l component), and the contracted x^l function is
+ *     rescaled to unit self-overlap; other components are not rescaled.
+ *   - Device work is enqueued on the caller's stream (a cudaStream_t passed as
+ *     ltjk_stream; NULL = legacy default stream) and the call returns without
+ *     waiting unless stated otherwise.  Input arrays must stay valid and
+ *     unmodified, and outputs must not be read, until the stream reaches the
+ *     point of the call.
+ *   - A context is not thread-safe: calls on one context from several host
+ *     threads must be serialised by the caller.  Distinct contexts are
+ *     independent.
+ */
+#ifndef LTJK_H
+#define LTJK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define LTJK_OK 0
+#define LTJK_EINVAL (-1)        /* invalid argument (null pointer, bad size, bad basis) */
+#define LTJK_ENOMEM (-2)        /* device or host allocation failed */
+#define LTJK_EBUDGET (-3)       /* request does not fit the service's HBM budget */
+#define LTJK_EUNSUPPORTED (-4)  /* angular momentum above the compiled maximum */
+#define LTJK_ECUDA (-5)         /* a CUDA runtime call failed */
+#define LTJK_ETIMEDOUT (-6)     /* a bounded wait ran out */
+#define LTJK_ECANCELLED (-7)    /* the request was cancelled */
+#define LTJK_ENOTREADY (-8)     /* result not yet available */
+
+#define LTJK_MAX_L 2            /* largest shell angular momentum of the value build */
+
+#define LTJK_FP64 0
+#define LTJK_MIXED 1
+
+typedef struct CUstream_st *ltjk_stream;
+
+/* Thread-local description of the last failure on this host thread. */
+const char *ltjk_last_error(void);
+
+/* Library version, MAJOR*10000 + MINOR*100 + PATCH. */
+int ltjk_version(void);
+
+/* --------------------------------------------------------------- contexts */
+/* A molecule in a Cartesian contracted Gaussian basis.  All arrays are host
+   arrays and are copied by ltjk_context_create.
+     natoms, coords_host[natoms*3]      atom positions, bohr
+     nshells                            number of shells
+     shell_atom_host[nshells]           atom index of each shell (0..natoms-1)
+     shell_l_host[nshells]              angular momentum, 0..LTJK_MAX_L
+     shell_nprim_host[nshells]          number of primitives, 1..8
+     exps_host[sum nprim]               primitive exponents (> 0), shell by shell
+     coefs_host[sum nprim]              contraction coefficients with respect to
+                                        unit-normalised primitives (see above) */
+typedef struct {
+  int natoms;
+  const double *coords_host;
+  int nshells;
+  const int *shell_atom_host;
+  const int *shell_l_host;
+  const int *shell_nprim_host;
+  const double *exps_host;
+  const double *coefs_host;
+} ltjk_basis;
+
+/* Build options.
+     schwarz_tau  shell quartet (ab|cd) is skipped iff Q_ab * Q_cd < schwarz_tau,
+                  Q_ab = max over mu in a, nu in b of sqrt|(mu nu|mu nu)|
+                  (plain Schwarz bound, not density weighted).  0 keeps all.
+     mixed_tau    precision == LTJK_MIXED only: quartets with Q_ab*Q_cd > mixed_tau
+                  are evaluated in FP64, the rest in FP32 (Boys function always
+                  FP64; J/K always accumulated in FP64).
+     precision    LTJK_FP64 or LTJK_MIXED.
+     device       CUDA device ordinal the context lives on. */
+typedef struct {
+  double schwarz_tau;
+  double mixed_tau;
+  int precision;
+  int device;
+} ltjk_opts;
+
+typedef struct ltjk_ctx ltjk_ctx;
+
+/* Work counts of a context (host values). */
+typedef struct {
+  int nao;
+  int nshells;
+  int npairs;                 /* shell pairs a >= b */
+  int64_t quartets_total;     /* unique shell quartets before screening */
+  int64_t quartets_kept;      /* unique shell quartets kept by Schwarz */
+  int64_t quartets_fp64;      /* of those, evaluated in FP64 */
+  int64_t prim_quartets_kept; /* primitive quartets over the kept shell quartets */
+  int64_t cart_integrals_kept;/* contracted Cartesian integrals over the kept quartets */
+  double eri_flops_per_build; /* recurrence flop model over the kept quartets */
+  size_t device_bytes;        /* device memory held by the context */
+} ltjk_ctx_stats;
+
+/* Create a context: normalises the basis, builds every shell pair and its
+   primitive-pair data, evaluates the Schwarz factors on the device, sorts the
+   pairs by class and Q and builds the screened quartet work lists (Schwarz
+   screening, cf. the paper's Sect. "Cost" and its screening discussion).
+   Synchronous.  *out receives the context. */
+int ltjk_context_create(const ltjk_basis *basis, const ltjk_opts *opts, ltjk_ctx **out);
+int ltjk_context_destroy(ltjk_ctx *ctx);
+int ltjk_nao(const ltjk_ctx *ctx, int *nao);
+int ltjk_context_stats(const ltjk_ctx *ctx, ltjk_ctx_stats *out);
+
+/* Schwarz factors of every ordered shell pair, Q_host[a*nshells + b]. Synchronous. */
+int ltjk_schwarz(const ltjk_ctx *ctx, double *Q_host);
+
+/* ------------------------------------------------------ Laplace quadrature */
+/* Least-squares exponential sum sum_q w_q exp(-t_q x) ~ 1/x on [xmin, xmax]
+   (Eq. laplace), fitted on the relative residual by Levenberg-Marquardt with
+   continuation in the number of points.  Host-only, synchronous.
+     0 < xmin < xmax, 1 <= n <= 32; t_host[n], w_host[n] receive the nodes
+     (ascending) and weights; *max_rel_err (nullable) receives
+     max |x sum w exp(-t x) - 1| on 10^5 log-spaced points of [xmin, xmax]. */
+int ltjk_laplace_quadrature(double xmin, double xmax, int n, double *t_host, double *w_host,
+                            double *max_rel_err);
+
+/* --------------------------------------------------------- pseudo-densities */
+/* D[q*npair + p] = U_q X_p V_q^T, U_q = C_occ diag(exp(+t_q eps_occ)),
+   V_q = C_vir diag(exp(-t_q eps_vir)) (Eq. scaledcoeff; Eq. aodensk with the
+   residual replaced by the transition amplitudes X_p).  No quadrature weight is
+   applied.
+     C_occ [N][nocc], C_vir [N][nvir], eps_occ [nocc], eps_vir [nvir] (device),
+     X [npair][nocc][nvir] (device), t_host [nlap] (host),
+     D [nlap*npair][N][N] (device, overwritten). */
+int ltjk_pseudo_densities(ltjk_ctx *ctx, int nocc, int nvir, const double *C_occ,
+                          const double *C_vir, const double *eps_occ, const double *eps_vir,
+                          int npair, const double *X, int nlap, const double *t_host, double *D,
+                          ltjk_stream stream);
+
+/* ------------------------------------------------------------- J/K build */
+/* J[q]_{mu nu} = sum_{ka rho} (mu nu|ka rho) D[q]_{ka rho},
+   K[q]_{mu nu} = sum_{ka rho} (mu ka|nu rho) D[q]_{ka rho}   (Eq. jkbuild)
+   for ndens arbitrary (non-symmetric) D[q], over the Schwarz-kept quartets,
+   ERIs recomputed on the fly in the context's precision.
+     D [ndens][N][N] in; J, K [ndens][N][N] out (overwritten; either may be
+     NULL to skip it).  1 <= ndens <= 4096.  Uses internal device scratch
+     (held by the context, grown on demand). */
+int ltjk_jk_build(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *K,
+                  ltjk_stream stream);
+
+/* ---------------------------------------------------------- gradient adjoint */
+/* grad[A][x] = d/dR_{A,x} sum_r [cJ J(P_r, Q_r) + cK K(P_r, Q_r)] with the
+   ordered builds J(A,B) = sum (mu nu|ka rho) A_{mu nu} B_{ka rho} and
+   K(A,B) = sum (mu ka|nu rho) A_{mu nu} B_{ka rho} (Eq. jkderiv); derivative
+   integrals for three centres, the fourth by translational invariance
+   (Eq. l18).  Only the two-electron term: no one-electron or nuclear part.
+     P, Q [nterms][N][N] (device, any symmetry), grad [natoms][3] (device,
+     overwritten).  1 <= nterms <= 4096. */
+int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, double cJ,
+                 double cK, double *grad, ltjk_stream stream);
+
+/* ------------------------------------------------------------- inspection */
+/* Contracted Cartesian integral blocks of nq shell quartets (a,b|c,d) given in
+   shells_host[4*nq]; out [sum of block sizes] device FP64, blocks concatenated
+   in order, each [na][nb][nc][nd] row-major.  Evaluated by the same kernels as
+   the build, in FP64 (precision = LTJK_FP64) or FP32 (LTJK_MIXED). */
+int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int precision,
+                        double *out, ltjk_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LTJK_H */

@@ -1,0 +1,731 @@
+// C-ABI entry points of the library (include/ltjk.h): contexts, shell pairs and
+// Schwarz screening, work lists, the J/K build, the gradient adjoint, the
+// pseudo-densities and the inspection call.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "host.h"
+#include "kernels.cuh"
+
+using namespace ltjk;
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return set_error(LTJK_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));      \
+  } while (0)
+
+namespace {
+
+constexpr int kKetChunk = 16;            // ket pairs per work item
+constexpr int kSmemBudget = 200 * 1024;  // bytes of shared memory per CTA we plan for
+constexpr int kMaxSmem = 227 * 1024;
+constexpr double kPrimPairDrop = 1e-18;  // drop primitive pair iff K_AB |c_a c_b| below this
+
+// Device buffer owned by a context.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  int alloc(size_t n) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    if (n == 0) return LTJK_OK;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return set_error(LTJK_ENOMEM, "cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
+    }
+    bytes = n;
+    return LTJK_OK;
+  }
+  template <typename T>
+  int upload(const std::vector<T> &v) {
+    int rc = alloc(v.size() * sizeof(T));
+    if (rc) return rc;
+    if (!v.empty()) CUDA_TRY(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return LTJK_OK;
+  }
+  template <typename T>
+  T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct ClassWork {
+  int X, Y;            // bra and ket pair class
+  int la, lb, lc, ld;
+  int ket_base;        // first pair of class Y in the sorted pair array
+  DevBuf items64, items32;
+  int n64 = 0, n32 = 0;
+};
+
+// Programs are generated once per process and uploaded once per device.
+struct ProgramCache {
+  std::mutex mu;
+  bool built = false;
+  ProgramSet ps;
+  std::map<int, std::shared_ptr<DevBuf>> vrr, hrr, acc, lev, tiles, boys;
+};
+ProgramCache g_prog;
+
+int program_set(const ProgramSet **ps) {
+  std::lock_guard<std::mutex> g(g_prog.mu);
+  if (!g_prog.built) {
+    try {
+      build_programs(g_prog.ps);
+    } catch (const std::exception &e) {
+      return set_error(LTJK_EINVAL, "program generation failed: %s", e.what());
+    }
+    g_prog.built = true;
+  }
+  *ps = &g_prog.ps;
+  return LTJK_OK;
+}
+
+int device_programs(int dev, DevProgs *out, const double **boys) {
+  const ProgramSet *ps;
+  int rc = program_set(&ps);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> g(g_prog.mu);
+  if (!g_prog.vrr.count(dev)) {
+    auto v = std::make_shared<DevBuf>(), h = std::make_shared<DevBuf>(),
+         a = std::make_shared<DevBuf>(), l = std::make_shared<DevBuf>(),
+         t = std::make_shared<DevBuf>(), b = std::make_shared<DevBuf>();
+    if ((rc = v->upload(ps->vrr)) || (rc = h->upload(ps->hrr)) || (rc = a->upload(ps->acc)) ||
+        (rc = l->upload(ps->levels)) || (rc = t->upload(ps->tiles)))
+      return rc;
+    std::vector<double> tab((size_t)kBoysRows * kBoysCols);
+    boys_table(kBoysRows, kBoysCols, kBoysStep, tab.data());
+    if ((rc = b->upload(tab))) return rc;
+    double inv_odd[kBoysCols + 2], inv_int[kBoysTaylor + 1];
+    for (int m = 0; m < kBoysCols + 2; ++m) inv_odd[m] = 1.0 / (2 * m + 1);
+    inv_int[0] = 0.0;
+    for (int j = 1; j <= kBoysTaylor; ++j) inv_int[j] = 1.0 / j;
+    CUDA_TRY(cudaMemcpyToSymbol(c_inv_odd, inv_odd, sizeof(inv_odd)));
+    CUDA_TRY(cudaMemcpyToSymbol(c_inv_int, inv_int, sizeof(inv_int)));
+    g_prog.vrr[dev] = v;
+    g_prog.hrr[dev] = h;
+    g_prog.acc[dev] = a;
+    g_prog.lev[dev] = l;
+    g_prog.tiles[dev] = t;
+    g_prog.boys[dev] = b;
+  }
+  out->vrr = g_prog.vrr[dev]->as<VrrInstr>();
+  out->hrr = g_prog.hrr[dev]->as<HrrInstr>();
+  out->acc = g_prog.acc[dev]->as<AccInstr>();
+  out->levels = g_prog.lev[dev]->as<int>();
+  out->tiles = g_prog.tiles[dev]->as<TileProg>();
+  *boys = g_prog.boys[dev]->as<double>();
+  return LTJK_OK;
+}
+
+// Launch configuration of one class program: groups per warp from the average
+// width of a recurrence level, warps per CTA from the shared-memory budget.
+ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
+  ClassLaunch cl{};
+  cl.p = p;
+  int ninstr = 0;
+  const ProgramSet &ps = g_prog.ps;
+  if (p.nvrr_level > 0)
+    ninstr = ps.levels[p.vrr_level0 + p.nvrr_level] - ps.levels[p.vrr_level0];
+  double width = p.nvrr_level > 0 ? double(ninstr) / p.nvrr_level : 0.0;
+  int S = 1;
+  while (S < 32 && S < width) S *= 2;
+  cl.G = 32 / S;
+  for (;;) {
+    size_t bytes = warp_smem_bytes(p, cl.G, real_bytes);
+    cl.smem_per_warp = (int)bytes;
+    if (bytes <= (size_t)kSmemBudget || cl.G == 1) break;
+    cl.G /= 2;
+  }
+  cl.warps = std::max(1, std::min(4, kSmemBudget / std::max(cl.smem_per_warp, 1)));
+  return cl;
+}
+
+template <typename Real, int MODE>
+int launch_class(const DevBasis &B, const DevProgs &PR, const ClassLaunch &cl, const WorkItem *items,
+                 int nitems, int ket_base, const JKArgs &a, cudaStream_t st) {
+  if (nitems <= 0) return LTJK_OK;
+  const size_t smem = (size_t)cl.smem_per_warp * cl.warps;
+  if (smem > (size_t)kMaxSmem)
+    return set_error(LTJK_EUNSUPPORTED, "class (%d%d|%d%d) needs %zu bytes of shared memory",
+                     cl.p.la, cl.p.lb, cl.p.lc, cl.p.ld, smem);
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    CUDA_TRY(cudaFuncSetAttribute(quartet_kernel<Real, MODE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    attr_set = true;
+  }
+  const int ctas_needed = (nitems + cl.warps - 1) / cl.warps;
+  const int grid = std::min(ctas_needed, 152 * 32);
+  quartet_kernel<Real, MODE><<<grid, 32 * cl.warps, smem, st>>>(B, PR, cl, items, nitems, ket_base, a);
+  CUDA_TRY(cudaGetLastError());
+  return LTJK_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct ltjk_ctx {
+  int device = 0;
+  ltjk_opts opts{};
+  int natoms = 0, nshells = 0, nao = 0, npairs = 0;
+  std::vector<double> coords;
+  std::vector<int> sh_l, sh_atom, sh_ao, sh_nprim, sh_p0;
+  std::vector<double> exps, ncoef;
+  // sorted pairs
+  std::vector<int2> pair_sh;
+  std::vector<double> pair_Q;
+  std::vector<int> class_begin;  // pair index range of each pair class
+  std::map<std::pair<int, int>, int> pair_of;  // canonical (a,b) -> sorted pair index
+  // device data
+  DevBuf d_ctr, d_l, d_ao, d_atom, d_pair_sh, d_pair_pp0, d_pair_npp, d_pp_zeta, d_pp_izeta, d_pp_P,
+      d_pp_pref, d_pp_a, d_pp_b;
+  DevProgs progs{};
+  const double *boys = nullptr;
+  std::vector<std::unique_ptr<ClassWork>> work;       // value build
+  std::vector<std::unique_ptr<ClassWork>> work_grad;  // gradient (same screening)
+  DevBuf scratch;
+  DevBuf d_t;
+  ltjk_ctx_stats stats{};
+
+  DevBasis basis() const {
+    DevBasis B{};
+    B.sh_ctr = d_ctr.as<double>();
+    B.sh_l = d_l.as<int>();
+    B.sh_ao = d_ao.as<int>();
+    B.sh_atom = d_atom.as<int>();
+    B.pair_sh = d_pair_sh.as<int2>();
+    B.pair_pp0 = d_pair_pp0.as<int>();
+    B.pair_npp = d_pair_npp.as<int>();
+    B.pp_zeta = d_pp_zeta.as<double>();
+    B.pp_inv_zeta = d_pp_izeta.as<double>();
+    B.pp_P = d_pp_P.as<double>();
+    B.pp_pref = d_pp_pref.as<double>();
+    B.pp_a = d_pp_a.as<double>();
+    B.pp_b = d_pp_b.as<double>();
+    B.boys = boys;
+    B.nao = nao;
+    return B;
+  }
+  int ensure_scratch(size_t bytes) {
+    if (scratch.bytes >= bytes) return LTJK_OK;
+    // the previous contents are dead: callers order their use on one stream and
+    // the old buffer is released only after the device is idle
+    CUDA_TRY(cudaDeviceSynchronize());
+    return scratch.alloc(bytes + bytes / 4);
+  }
+};
+
+namespace {
+
+struct HostPairs {
+  std::vector<int2> sh;
+  std::vector<int> cls, pp0, npp;
+  std::vector<double> zeta, izeta, P, pref, a, b;
+};
+
+void build_pairs(const ltjk_ctx &c, const std::vector<int2> &order, HostPairs &hp) {
+  const double pi = 3.14159265358979323846;
+  const double s2pi52 = std::sqrt(2.0 * std::pow(pi, 2.5));
+  hp = HostPairs{};
+  for (const int2 &pr : order) {
+    const int sa = pr.x, sb = pr.y;
+    const double *A = &c.coords[3 * c.sh_atom[sa]], *B = &c.coords[3 * c.sh_atom[sb]];
+    double AB2 = 0.0;
+    for (int x = 0; x < 3; ++x) AB2 += (A[x] - B[x]) * (A[x] - B[x]);
+    hp.sh.push_back(pr);
+    hp.pp0.push_back((int)hp.zeta.size());
+    int kept = 0;
+    for (int i = 0; i < c.sh_nprim[sa]; ++i)
+      for (int j = 0; j < c.sh_nprim[sb]; ++j) {
+        const double al = c.exps[c.sh_p0[sa] + i], be = c.exps[c.sh_p0[sb] + j];
+        const double ca = c.ncoef[c.sh_p0[sa] + i], cb = c.ncoef[c.sh_p0[sb] + j];
+        const double z = al + be;
+        const double kab = std::exp(-al * be / z * AB2);
+        if (kab * std::fabs(ca * cb) < kPrimPairDrop) continue;
+        hp.zeta.push_back(z);
+        hp.izeta.push_back(1.0 / z);
+        for (int x = 0; x < 3; ++x) hp.P.push_back((al * A[x] + be * B[x]) / z);
+        hp.pref.push_back(s2pi52 * kab * ca * cb / z);
+        hp.a.push_back(al);
+        hp.b.push_back(be);
+        ++kept;
+      }
+    hp.npp.push_back(kept);
+  }
+}
+
+int upload_pairs(ltjk_ctx &c, const HostPairs &hp) {
+  int rc;
+  std::vector<int> pair_shx;
+  if ((rc = c.d_pair_sh.upload(hp.sh)) || (rc = c.d_pair_pp0.upload(hp.pp0)) ||
+      (rc = c.d_pair_npp.upload(hp.npp)) || (rc = c.d_pp_zeta.upload(hp.zeta)) ||
+      (rc = c.d_pp_izeta.upload(hp.izeta)) || (rc = c.d_pp_P.upload(hp.P)) ||
+      (rc = c.d_pp_pref.upload(hp.pref)) || (rc = c.d_pp_a.upload(hp.a)) ||
+      (rc = c.d_pp_b.upload(hp.b)))
+    return rc;
+  return LTJK_OK;
+}
+
+// Evaluate contracted blocks (pair i | pair j) for a list of (i, j) in `prec`.
+int store_blocks(ltjk_ctx &c, const std::vector<std::pair<int, int>> &qs, int prec,
+                 std::vector<long long> &offsets, double *d_out, cudaStream_t st) {
+  const ProgramSet *ps;
+  int rc = program_set(&ps);
+  if (rc) return rc;
+  // group by class
+  std::map<int, std::vector<int>> by_class;
+  offsets.assign(qs.size(), 0);
+  long long off = 0;
+  for (size_t k = 0; k < qs.size(); ++k) {
+    const int2 ab = c.pair_sh[qs[k].first], cd = c.pair_sh[qs[k].second];
+    const int qi = quartet_index(c.sh_l[ab.x], c.sh_l[ab.y], c.sh_l[cd.x], c.sh_l[cd.y], 0);
+    by_class[qi].push_back((int)k);
+    offsets[k] = off;
+    off += (long long)ps->progs[qi].nout * ps->progs[qi].ntile;
+  }
+  DevBasis B = c.basis();
+  for (auto &kv : by_class) {
+    const ClassProg &p = ps->progs[kv.first];
+    std::vector<WorkItem> items;
+    std::vector<long long> ioff;
+    for (int k : kv.second) {
+      items.push_back(WorkItem{qs[k].first, qs[k].second, 1, 0});
+      ioff.push_back(offsets[k]);
+    }
+    DevBuf d_items, d_off;
+    if ((rc = d_items.upload(items)) || (rc = d_off.upload(ioff))) return rc;
+    JKArgs a{};
+    a.out = d_out;
+    a.out_off = d_off.as<long long>();
+    if (prec == LTJK_FP64) {
+      ClassLaunch cl = make_launch(p, sizeof(double));
+      rc = launch_class<double, kStore>(B, c.progs, cl, d_items.as<WorkItem>(), (int)items.size(), 0,
+                                        a, st);
+    } else {
+      ClassLaunch cl = make_launch(p, sizeof(float));
+      rc = launch_class<float, kStore>(B, c.progs, cl, d_items.as<WorkItem>(), (int)items.size(), 0,
+                                       a, st);
+    }
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(st));  // the temporary item lists die here
+  }
+  return LTJK_OK;
+}
+
+// Flop model of a class (per contracted quartet with npq primitive quartets).
+double class_flops(const ClassProg &p, long long npq) {
+  const double boys = 40.0;
+  return npq * (p.vrr_flops + boys + 30.0 + 2.0 * p.nacc) + p.hrr_flops;
+}
+
+int build_work(ltjk_ctx &c) {
+  const ProgramSet *ps;
+  int rc = program_set(&ps);
+  if (rc) return rc;
+  const double tau = c.opts.schwarz_tau;
+  const bool mixed = c.opts.precision == LTJK_MIXED;
+  const double tmix = c.opts.mixed_tau;
+  c.work.clear();
+  c.work_grad.clear();
+  c.stats.quartets_total = 0;
+  c.stats.quartets_kept = 0;
+  c.stats.quartets_fp64 = 0;
+  c.stats.prim_quartets_kept = 0;
+  c.stats.cart_integrals_kept = 0;
+  c.stats.eri_flops_per_build = 0;
+  std::vector<int> npp_host(c.npairs);
+  {
+    // primitive pair counts are needed for the statistics
+    std::vector<int> tmp(c.npairs);
+    CUDA_TRY(cudaMemcpy(tmp.data(), c.d_pair_npp.p, sizeof(int) * c.npairs, cudaMemcpyDeviceToHost));
+    npp_host = tmp;
+  }
+  for (int X = 0; X < kNumPairClass; ++X)
+    for (int Y = 0; Y <= X; ++Y) {
+      const int xb = c.class_begin[X], xe = c.class_begin[X + 1];
+      const int yb = c.class_begin[Y], ye = c.class_begin[Y + 1];
+      if (xb == xe || yb == ye) continue;
+      auto cw = std::make_unique<ClassWork>();
+      cw->X = X;
+      cw->Y = Y;
+      const int2 s0 = c.pair_sh[xb], t0 = c.pair_sh[yb];
+      cw->la = c.sh_l[s0.x];
+      cw->lb = c.sh_l[s0.y];
+      cw->lc = c.sh_l[t0.x];
+      cw->ld = c.sh_l[t0.y];
+      cw->ket_base = yb;
+      const ClassProg &p = ps->progs[quartet_index(cw->la, cw->lb, cw->lc, cw->ld, 0)];
+      std::vector<WorkItem> i64, i32;
+      for (int i = xb; i < xe; ++i) {
+        const double qi = c.pair_Q[i];
+        int nj = ye - yb;
+        if (X == Y) nj = i - xb + 1;
+        c.stats.quartets_total += nj;
+        // prefix of kets with Q_i Q_j >= tau (Q sorted descending)
+        int lo = 0, hi = nj;
+        while (lo < hi) {
+          int mid = (lo + hi) / 2;
+          if (qi * c.pair_Q[yb + mid] >= tau) lo = mid + 1; else hi = mid;
+        }
+        const int nkeep = lo;
+        int n64 = nkeep;
+        if (mixed) {
+          lo = 0;
+          hi = nkeep;
+          while (lo < hi) {
+            int mid = (lo + hi) / 2;
+            if (qi * c.pair_Q[yb + mid] > tmix) lo = mid + 1; else hi = mid;
+          }
+          n64 = lo;
+        }
+        for (int k = 0; k < n64; k += kKetChunk) i64.push_back({i, k, std::min(kKetChunk, n64 - k), 0});
+        for (int k = n64; k < nkeep; k += kKetChunk)
+          i32.push_back({i, k, std::min(kKetChunk, nkeep - k), 0});
+        c.stats.quartets_kept += nkeep;
+        c.stats.quartets_fp64 += n64;
+        long long npq = 0;
+        for (int j = 0; j < nkeep; ++j) npq += (long long)npp_host[i] * npp_host[yb + j];
+        c.stats.prim_quartets_kept += npq;
+        c.stats.cart_integrals_kept +=
+            (long long)nkeep * ncart(cw->la) * ncart(cw->lb) * ncart(cw->lc) * ncart(cw->ld);
+        c.stats.eri_flops_per_build += class_flops(p, npq) + (double)nkeep * 0.0;
+      }
+      if ((rc = cw->items64.upload(i64)) || (rc = cw->items32.upload(i32))) return rc;
+      cw->n64 = (int)i64.size();
+      cw->n32 = (int)i32.size();
+      c.work.push_back(std::move(cw));
+    }
+  return LTJK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ltjk_last_error(void) { return last_error(); }
+int ltjk_version(void) { return 100; }
+
+int ltjk_context_create(const ltjk_basis *bs, const ltjk_opts *opts, ltjk_ctx **out) {
+  if (!bs || !opts || !out) return set_error(LTJK_EINVAL, "context_create: null argument");
+  *out = nullptr;
+  if (bs->natoms <= 0 || bs->nshells <= 0 || !bs->coords_host || !bs->shell_atom_host ||
+      !bs->shell_l_host || !bs->shell_nprim_host || !bs->exps_host || !bs->coefs_host)
+    return set_error(LTJK_EINVAL, "context_create: empty or incomplete basis");
+  if (opts->precision != LTJK_FP64 && opts->precision != LTJK_MIXED)
+    return set_error(LTJK_EINVAL, "context_create: precision must be LTJK_FP64 or LTJK_MIXED");
+  if (!(opts->schwarz_tau >= 0) || !(opts->mixed_tau >= 0))
+    return set_error(LTJK_EINVAL, "context_create: thresholds must be >= 0");
+  auto c = std::make_unique<ltjk_ctx>();
+  c->opts = *opts;
+  c->device = opts->device;
+  CUDA_TRY(cudaSetDevice(c->device));
+  c->natoms = bs->natoms;
+  c->nshells = bs->nshells;
+  c->coords.assign(bs->coords_host, bs->coords_host + 3 * bs->natoms);
+  int np = 0;
+  for (int s = 0; s < bs->nshells; ++s) {
+    const int l = bs->shell_l_host[s], n = bs->shell_nprim_host[s], at = bs->shell_atom_host[s];
+    if (l < 0) return set_error(LTJK_EINVAL, "shell %d: negative angular momentum", s);
+    if (l > kMaxL)
+      return set_error(LTJK_EUNSUPPORTED, "shell %d: l = %d above LTJK_MAX_L = %d", s, l, kMaxL);
+    if (n < 1 || n > kMaxPrim) return set_error(LTJK_EINVAL, "shell %d: nprim %d not in 1..%d", s, n, kMaxPrim);
+    if (at < 0 || at >= bs->natoms) return set_error(LTJK_EINVAL, "shell %d: atom %d out of range", s, at);
+    c->sh_l.push_back(l);
+    c->sh_atom.push_back(at);
+    c->sh_nprim.push_back(n);
+    c->sh_p0.push_back(np);
+    c->sh_ao.push_back(c->nao);
+    c->nao += ncart(l);
+    np += n;
+  }
+  c->exps.assign(bs->exps_host, bs->exps_host + np);
+  for (double e : c->exps)
+    if (!(e > 0) || !std::isfinite(e)) return set_error(LTJK_EINVAL, "non-positive primitive exponent");
+  for (int t = 0; t < 3 * bs->natoms; ++t)
+    if (!std::isfinite(c->coords[t])) return set_error(LTJK_EINVAL, "non-finite coordinate");
+  c->ncoef.resize(np);
+  for (int s = 0; s < c->nshells; ++s)
+    normalise_shell(c->sh_l[s], c->sh_nprim[s], &c->exps[c->sh_p0[s]], bs->coefs_host + c->sh_p0[s],
+                    &c->ncoef[c->sh_p0[s]]);
+  int rc;
+  if ((rc = device_programs(c->device, &c->progs, &c->boys))) return rc;
+  std::vector<double> ctr(3 * c->nshells);
+  for (int s = 0; s < c->nshells; ++s)
+    for (int x = 0; x < 3; ++x) ctr[3 * s + x] = c->coords[3 * c->sh_atom[s] + x];
+  if ((rc = c->d_ctr.upload(ctr)) || (rc = c->d_l.upload(c->sh_l)) || (rc = c->d_ao.upload(c->sh_ao)) ||
+      (rc = c->d_atom.upload(c->sh_atom)))
+    return rc;
+  // canonical pairs grouped by class: l_a >= l_b, and a >= b when l_a == l_b
+  std::vector<std::vector<int2>> by_class(kNumPairClass);
+  for (int a = 0; a < c->nshells; ++a)
+    for (int b = 0; b < c->nshells; ++b) {
+      const int la = c->sh_l[a], lb = c->sh_l[b];
+      if (la < lb || (la == lb && a < b)) continue;
+      by_class[pair_class(la, lb)].push_back(make_int2(a, b));
+    }
+  std::vector<int2> order;
+  for (auto &v : by_class) order.insert(order.end(), v.begin(), v.end());
+  c->npairs = (int)order.size();
+  HostPairs hp;
+  build_pairs(*c, order, hp);
+  c->pair_sh = order;
+  if ((rc = upload_pairs(*c, hp))) return rc;
+  // Schwarz factors from the diagonal quartets (ab|ab), evaluated in FP64
+  {
+    std::vector<std::pair<int, int>> qs;
+    for (int i = 0; i < c->npairs; ++i) qs.push_back({i, i});
+    const ProgramSet *ps;
+    if ((rc = program_set(&ps))) return rc;
+    long long total = 0;
+    for (int i = 0; i < c->npairs; ++i) {
+      const int2 ab = order[i];
+      total += (long long)ncart(c->sh_l[ab.x]) * ncart(c->sh_l[ab.y]) * ncart(c->sh_l[ab.x]) *
+               ncart(c->sh_l[ab.y]);
+    }
+    DevBuf d_out;
+    if ((rc = d_out.alloc(sizeof(double) * std::max<long long>(total, 1)))) return rc;
+    std::vector<long long> offs;
+    if ((rc = store_blocks(*c, qs, LTJK_FP64, offs, d_out.as<double>(), 0))) return rc;
+    std::vector<double> blocks(total);
+    CUDA_TRY(cudaMemcpy(blocks.data(), d_out.p, sizeof(double) * total, cudaMemcpyDeviceToHost));
+    c->pair_Q.assign(c->npairs, 0.0);
+    for (int i = 0; i < c->npairs; ++i) {
+      const int na = ncart(c->sh_l[order[i].x]), nb = ncart(c->sh_l[order[i].y]);
+      double m = 0.0;
+      for (int x = 0; x < na; ++x)
+        for (int y = 0; y < nb; ++y) {
+          const double v = std::fabs(blocks[offs[i] + ((x * nb + y) * na + x) * nb + y]);
+          m = std::max(m, v);
+        }
+      c->pair_Q[i] = std::sqrt(m);
+    }
+  }
+  // sort each class by Q descending and rebuild the pair data in that order
+  {
+    std::vector<int2> sorted;
+    std::vector<double> qsorted;
+    c->class_begin.assign(kNumPairClass + 1, 0);
+    int base = 0;
+    for (int X = 0; X < kNumPairClass; ++X) {
+      const int n = (int)by_class[X].size();
+      std::vector<int> idx(n);
+      for (int k = 0; k < n; ++k) idx[k] = base + k;
+      std::stable_sort(idx.begin(), idx.end(), [&](int u, int v) { return c->pair_Q[u] > c->pair_Q[v]; });
+      c->class_begin[X] = (int)sorted.size();
+      for (int k : idx) {
+        sorted.push_back(order[k]);
+        qsorted.push_back(c->pair_Q[k]);
+      }
+      base += n;
+    }
+    c->class_begin[kNumPairClass] = (int)sorted.size();
+    c->pair_sh = sorted;
+    c->pair_Q = qsorted;
+    build_pairs(*c, sorted, hp);
+    if ((rc = upload_pairs(*c, hp))) return rc;
+    for (int i = 0; i < c->npairs; ++i) c->pair_of[{sorted[i].x, sorted[i].y}] = i;
+  }
+  if ((rc = build_work(*c))) return rc;
+  c->stats.nao = c->nao;
+  c->stats.nshells = c->nshells;
+  c->stats.npairs = c->npairs;
+  *out = c.release();
+  return LTJK_OK;
+}
+
+int ltjk_context_destroy(ltjk_ctx *ctx) {
+  if (!ctx) return set_error(LTJK_EINVAL, "context_destroy: null context");
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  delete ctx;
+  return LTJK_OK;
+}
+
+int ltjk_nao(const ltjk_ctx *ctx, int *nao) {
+  if (!ctx || !nao) return set_error(LTJK_EINVAL, "nao: null argument");
+  *nao = ctx->nao;
+  return LTJK_OK;
+}
+
+int ltjk_context_stats(const ltjk_ctx *ctx, ltjk_ctx_stats *out) {
+  if (!ctx || !out) return set_error(LTJK_EINVAL, "context_stats: null argument");
+  *out = ctx->stats;
+  size_t b = 0;
+  for (const DevBuf *d : {&ctx->d_ctr, &ctx->d_l, &ctx->d_ao, &ctx->d_atom, &ctx->d_pair_sh,
+                          &ctx->d_pair_pp0, &ctx->d_pair_npp, &ctx->d_pp_zeta, &ctx->d_pp_izeta,
+                          &ctx->d_pp_P, &ctx->d_pp_pref, &ctx->d_pp_a, &ctx->d_pp_b, &ctx->scratch})
+    b += d->bytes;
+  for (auto &w : ctx->work) b += w->items64.bytes + w->items32.bytes;
+  out->device_bytes = b;
+  return LTJK_OK;
+}
+
+int ltjk_schwarz(const ltjk_ctx *ctx, double *Q_host) {
+  if (!ctx || !Q_host) return set_error(LTJK_EINVAL, "schwarz: null argument");
+  const int ns = ctx->nshells;
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b < ns; ++b) {
+      auto it = ctx->pair_of.find({a, b});
+      if (it == ctx->pair_of.end()) it = ctx->pair_of.find({b, a});
+      Q_host[a * ns + b] = ctx->pair_Q[it->second];
+    }
+  return LTJK_OK;
+}
+
+int ltjk_laplace_quadrature(double xmin, double xmax, int n, double *t_host, double *w_host,
+                            double *max_rel_err) {
+  return laplace_quadrature(xmin, xmax, n, t_host, w_host, max_rel_err);
+}
+
+int ltjk_jk_build(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *K,
+                  ltjk_stream stream) {
+  if (!ctx || !D) return set_error(LTJK_EINVAL, "jk_build: null context or density");
+  if (ndens < 1 || ndens > 4096) return set_error(LTJK_EINVAL, "jk_build: ndens %d not in 1..4096", ndens);
+  if (!J && !K) return LTJK_OK;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t NN = (size_t)ctx->nao * ctx->nao, n = NN * ndens;
+  int rc = ctx->ensure_scratch(4 * n * sizeof(double));
+  if (rc) return rc;
+  double *Dq = ctx->scratch.as<double>(), *Sq = Dq + n, *Jq = Sq + n, *Kq = Jq + n;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  to_qinner<<<blocks, 256, 0, st>>>(D, Dq, Sq, ndens, ctx->nao);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(Jq, 0, 2 * n * sizeof(double), st));
+  JKArgs a{};
+  a.D = Dq;
+  a.S = Sq;
+  a.J = J ? Jq : nullptr;
+  a.K = K ? Kq : nullptr;
+  a.nd = ndens;
+  DevBasis B = ctx->basis();
+  const ProgramSet *ps;
+  if ((rc = program_set(&ps))) return rc;
+  for (auto &w : ctx->work) {
+    const ClassProg &p = ps->progs[quartet_index(w->la, w->lb, w->lc, w->ld, 0)];
+    if (w->n64) {
+      ClassLaunch cl = make_launch(p, sizeof(double));
+      if ((rc = launch_class<double, kJK>(B, ctx->progs, cl, w->items64.as<WorkItem>(), w->n64,
+                                          w->ket_base, a, st)))
+        return rc;
+    }
+    if (w->n32) {
+      ClassLaunch cl = make_launch(p, sizeof(float));
+      if ((rc = launch_class<float, kJK>(B, ctx->progs, cl, w->items32.as<WorkItem>(), w->n32,
+                                         w->ket_base, a, st)))
+        return rc;
+    }
+  }
+  from_qinner<<<blocks, 256, 0, st>>>(Jq, Kq, J, K, ndens, ctx->nao);
+  CUDA_TRY(cudaGetLastError());
+  return LTJK_OK;
+}
+
+int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, double cJ, double cK,
+                 double *grad, ltjk_stream stream) {
+  if (!ctx || !P || !Q || !grad) return set_error(LTJK_EINVAL, "jk_grad: null argument");
+  if (nterms < 1 || nterms > 4096) return set_error(LTJK_EINVAL, "jk_grad: nterms %d not in 1..4096", nterms);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t NN = (size_t)ctx->nao * ctx->nao, n = NN * nterms;
+  int rc = ctx->ensure_scratch(2 * n * sizeof(double));
+  if (rc) return rc;
+  double *Pq = ctx->scratch.as<double>(), *Qq = Pq + n;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  to_qinner<<<blocks, 256, 0, st>>>(P, Pq, nullptr, nterms, ctx->nao);
+  to_qinner<<<blocks, 256, 0, st>>>(Q, Qq, nullptr, nterms, ctx->nao);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 3 * ctx->natoms, st));
+  JKArgs a{};
+  a.P = Pq;
+  a.Q = Qq;
+  a.nd = nterms;
+  a.cJ = cJ;
+  a.cK = cK;
+  a.grad = grad;
+  DevBasis B = ctx->basis();
+  const ProgramSet *ps;
+  if ((rc = program_set(&ps))) return rc;
+  for (auto &w : ctx->work) {
+    const ClassProg &p = ps->progs[quartet_index(w->la, w->lb, w->lc, w->ld, 1)];
+    if (w->n64) {
+      ClassLaunch cl = make_launch(p, sizeof(double));
+      if ((rc = launch_class<double, kGrad>(B, ctx->progs, cl, w->items64.as<WorkItem>(), w->n64,
+                                            w->ket_base, a, st)))
+        return rc;
+    }
+    if (w->n32) {
+      ClassLaunch cl = make_launch(p, sizeof(float));
+      if ((rc = launch_class<float, kGrad>(B, ctx->progs, cl, w->items32.as<WorkItem>(), w->n32,
+                                           w->ket_base, a, st)))
+        return rc;
+    }
+  }
+  return LTJK_OK;
+}
+
+int ltjk_pseudo_densities(ltjk_ctx *ctx, int nocc, int nvir, const double *C_occ,
+                          const double *C_vir, const double *eps_occ, const double *eps_vir,
+                          int npair, const double *X, int nlap, const double *t_host, double *D,
+                          ltjk_stream stream) {
+  if (!ctx || !C_occ || !C_vir || !eps_occ || !eps_vir || !X || !t_host || !D)
+    return set_error(LTJK_EINVAL, "pseudo_densities: null argument");
+  if (nocc < 1 || nvir < 1 || npair < 1 || nlap < 1 || (long long)npair * nlap > 4096)
+    return set_error(LTJK_EINVAL, "pseudo_densities: bad sizes");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int N = ctx->nao, nq = nlap * npair;
+  const size_t ny = (size_t)nq * nocc * nvir, nz = (size_t)nq * nocc * N;
+  int rc;
+  if (ctx->d_t.bytes < sizeof(double) * nlap && (rc = ctx->d_t.alloc(sizeof(double) * 64 * ((nlap + 63) / 64))))
+    return rc;
+  if ((rc = ctx->ensure_scratch((ny + nz) * sizeof(double)))) return rc;
+  double *Y = ctx->scratch.as<double>(), *Z = Y + ny;
+  CUDA_TRY(cudaMemcpyAsync(ctx->d_t.p, t_host, sizeof(double) * nlap, cudaMemcpyHostToDevice, st));
+  scale_amplitudes<<<(int)std::min<size_t>((ny + 255) / 256, 152 * 16), 256, 0, st>>>(
+      X, eps_occ, eps_vir, ctx->d_t.as<double>(), Y, nlap, npair, nocc, nvir);
+  dim3 thr(16, 16);
+  dim3 g1((N + 15) / 16, (nocc + 15) / 16, nq);
+  gemm_f64<true><<<g1, thr, 0, st>>>(Y, (long long)nocc * nvir, C_vir, 0, Z, (long long)nocc * N,
+                                     nocc, N, nvir, nvir, nvir, N);
+  dim3 g2((N + 15) / 16, (N + 15) / 16, nq);
+  gemm_f64<false><<<g2, thr, 0, st>>>(C_occ, 0, Z, (long long)nocc * N, D, (long long)N * N, N, N,
+                                      nocc, nocc, N, N);
+  CUDA_TRY(cudaGetLastError());
+  return LTJK_OK;
+}
+
+int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int precision, double *out,
+                        ltjk_stream stream) {
+  if (!ctx || !shells_host || !out || nq < 0) return set_error(LTJK_EINVAL, "shell_quartets: bad argument");
+  if (precision != LTJK_FP64 && precision != LTJK_MIXED)
+    return set_error(LTJK_EINVAL, "shell_quartets: bad precision");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  std::vector<std::pair<int, int>> qs;
+  for (int k = 0; k < nq; ++k) {
+    const int *s = shells_host + 4 * k;
+    for (int t = 0; t < 4; ++t)
+      if (s[t] < 0 || s[t] >= ctx->nshells) return set_error(LTJK_EINVAL, "shell_quartets: shell index");
+    auto i = ctx->pair_of.find({s[0], s[1]}), j = ctx->pair_of.find({s[2], s[3]});
+    if (i == ctx->pair_of.end() || j == ctx->pair_of.end())
+      return set_error(LTJK_EINVAL,
+                       "shell_quartets: pair (%d,%d) or (%d,%d) not in canonical order "
+                       "(l_a > l_b, or l_a == l_b and a >= b)",
+                       s[0], s[1], s[2], s[3]);
+    qs.push_back({i->second, j->second});
+  }
+  std::vector<long long> offs;
+  return store_blocks(*ctx, qs, precision, offs, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

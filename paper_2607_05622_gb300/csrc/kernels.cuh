@@ -1,0 +1,475 @@
+// Device code: Boys function, the warp-cooperative recurrence interpreter for
+// contracted shell quartets, and the fused J/K digestion and gradient
+// contraction.  Included by context.cu only.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ltjk_internal.h"
+
+namespace ltjk {
+
+// ------------------------------------------------------------------ Boys
+// F_m(T) = int_0^1 u^{2m} exp(-T u^2) du.  For T < kBoysTmax: 8-term Taylor
+// expansion of F_mmax about the nearest tabulated point (dF_m/dT = -F_{m+1}),
+// then the downward relation F_m = (2T F_{m+1} + e^{-T}) / (2m+1).  Otherwise
+// F_0 = (1/2) sqrt(pi/T) (erf(sqrt T) = 1 to double precision there) and the
+// upward relation F_{m+1} = ((2m+1) F_m - e^{-T}) / (2T).  The table is filled on
+// the host by Gauss-Legendre quadrature of the defining integral.
+constexpr double kBoysStep = 0.05;
+constexpr double kBoysInvStep = 20.0;
+constexpr double kBoysTmax = 40.0;
+constexpr int kBoysRows = 801;                 // T_k = k * step, k = 0..800
+constexpr int kBoysTaylor = 8;
+constexpr int kBoysCols = kBoysMaxM + kBoysTaylor;  // m = 0 .. kBoysMaxM + 7
+
+__constant__ double c_inv_odd[kBoysCols + 2];   // 1/(2m+1)
+__constant__ double c_inv_int[kBoysTaylor + 1]; // 1/j
+
+__device__ __forceinline__ void boys_eval(int mmax, double T, const double *__restrict__ tab,
+                                          double *F) {
+  if (T < kBoysTmax) {
+    int k = __double2int_rn(T * kBoysInvStep);
+    double x = k * kBoysStep - T;  // -(T - T_k)
+    const double *row = tab + k * kBoysCols + mmax;
+    double f = __ldg(row + kBoysTaylor - 1);
+#pragma unroll
+    for (int j = kBoysTaylor - 2; j >= 0; --j) f = fma(f, x * c_inv_int[j + 1], __ldg(row + j));
+    F[mmax] = f;
+    double e = exp(-T);
+    for (int m = mmax - 1; m >= 0; --m) F[m] = fma(2.0 * T, F[m + 1], e) * c_inv_odd[m];
+  } else {
+    double e = exp(-T);
+    double inv2T = 0.5 / T;
+    F[0] = 0.88622692545275801365 * rsqrt(T);  // (1/2) sqrt(pi/T)
+    for (int m = 0; m < mmax; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) * inv2T;
+  }
+}
+
+// --------------------------------------------------------------- layouts
+struct DevBasis {
+  // shells
+  const double *sh_ctr;  // [nshells][3]
+  const int *sh_l, *sh_ao, *sh_atom;
+  // shell pairs (a, b) sorted by class, then by Schwarz factor (descending)
+  const int2 *pair_sh;   // shells (a, b), l_a >= l_b
+  const int *pair_pp0;   // first primitive pair
+  const int *pair_npp;   // number of primitive pairs kept
+  // primitive pairs
+  const double *pp_zeta, *pp_inv_zeta, *pp_P, *pp_pref, *pp_a, *pp_b;  // pp_P: [npp][3]
+  const double *boys;    // [kBoysRows][kBoysCols]
+  int nao;
+};
+
+struct DevProgs {
+  const VrrInstr *vrr;
+  const HrrInstr *hrr;
+  const AccInstr *acc;
+  const int *levels;
+  const TileProg *tiles;
+};
+
+// Work item: bra pair, ket pairs [k0, k0 + nk).
+struct WorkItem {
+  int bra, k0, nk, pad;
+};
+
+enum Mode { kStore = 0, kJK = 1, kGrad = 2 };
+
+struct JKArgs {
+  // q-innermost layouts: X[(mu*N + nu)*nd + q]
+  const double *D;   // densities
+  const double *S;   // D + D^T
+  double *J;         // half-Coulomb accumulator (symmetrised afterwards)
+  double *K;
+  int nd;
+  // store mode
+  double *out;
+  const long long *out_off;  // per work item: offset of its first block
+  // gradient
+  const double *P, *Q;  // q-innermost term stacks, nd = nterms
+  double cJ, cK;
+  double *grad;         // [natoms][3]
+};
+
+// Per-primitive-quartet table entry layout (Real units):
+//   [0 .. ltot]           base values [00|00]^(m)
+//   [ltot+1 .. +kNumCoef) coefficients (CoefSlot order)
+//   then hz[0..nmax], he[0..nmax], hs[0..nmax]: n/(2 zeta), n/(2 eta), n/(2(zeta+eta))
+constexpr int kNmax = 2 * kMaxLDeriv + 2;  // largest integer multiplier + 1
+__host__ __device__ inline int pt_stride(int ltot) { return ltot + 1 + kNumCoef + 3 * kNmax; }
+
+struct ClassLaunch {
+  ClassProg p;
+  int G;        // primitive-quartet groups per warp (S = 32 / G lanes each)
+  int warps;    // warps per CTA
+  int smem_per_warp;  // bytes
+};
+
+// Shared memory one warp needs for class program p with G groups, in bytes:
+// primitive table, G accumulator sets and the work region (Real), then for
+// the gradient the Gamma block of one quartet (double).
+__host__ __device__ inline size_t warp_smem_bytes(const ClassProg &p, int G, size_t real_bytes) {
+  int work = G * p.vrr_size > p.hrr_size ? G * p.vrr_size : p.hrr_size;
+  size_t b = (size_t)(32 * pt_stride(p.ltot) + G * p.acc_total + work) * real_bytes;
+  b = (b + 15) / 16 * 16;
+  if (p.deriv) b += (size_t)p.nout * sizeof(double);
+  return (b + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t gamma_offset(const ClassProg &p, int G, size_t real_bytes) {
+  int work = G * p.vrr_size > p.hrr_size ? G * p.vrr_size : p.hrr_size;
+  size_t b = (size_t)(32 * pt_stride(p.ltot) + G * p.acc_total + work) * real_bytes;
+  return (b + 15) / 16 * 16;
+}
+
+// ------------------------------------------------ one contracted quartet
+// Computes the contracted block(s) of quartet (bra pair ip | ket pair jp) into
+// the warp's shared memory and returns a pointer to the output block (nout
+// Reals, row-major [na][nb][nc][nd], or 9 such blocks for derivatives).
+template <typename Real>
+__device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const ClassProg &p, int G,
+                               Real *sm, int ip, int jp, int lane) {
+  const int S = 32 / G, g = lane / S, s = lane % S;
+  const int stride = pt_stride(p.ltot);
+  Real *ptab = sm;                              // [32][stride]
+  Real *accs = ptab + 32 * stride;              // [G][acc_total]; group 0's last
+  Real *acc0 = accs + (G - 1) * p.acc_total;
+  Real *work = acc0 + p.acc_total;              // VRR regions / HRR slots
+  Real *my_acc = accs + (G - 1 - g) * p.acc_total;
+  Real *my_vrr = work + g * p.vrr_size;
+
+  const int2 sab = B.pair_sh[ip], scd = B.pair_sh[jp];
+  const double *A = B.sh_ctr + 3 * sab.x, *Bc = B.sh_ctr + 3 * sab.y;
+  const double *C = B.sh_ctr + 3 * scd.x, *Dc = B.sh_ctr + 3 * scd.y;
+  const int pp0 = B.pair_pp0[ip], npp = B.pair_npp[ip];
+  const int qq0 = B.pair_pp0[jp], nqq = B.pair_npp[jp];
+  const int npq = npp * nqq;
+
+  for (int t = lane; t < G * p.acc_total; t += 32) accs[t] = Real(0);
+
+  for (int c0 = 0; c0 < npq; c0 += 32) {
+    // stage 1: base values and coefficients, one primitive quartet per lane
+    const int pq = c0 + lane;
+    if (pq < npq) {
+      const int ia = pp0 + pq / nqq, ic = qq0 + pq % nqq;
+      const double zeta = B.pp_zeta[ia], eta = B.pp_zeta[ic];
+      const double izeta = B.pp_inv_zeta[ia], ieta = B.pp_inv_zeta[ic];
+      const double *P = B.pp_P + 3 * ia, *Q = B.pp_P + 3 * ic;
+      const double isum = 1.0 / (zeta + eta);
+      const double rho = zeta * eta * isum;
+      double PQ2 = 0.0, W[3];
+      for (int x = 0; x < 3; ++x) {
+        double d = P[x] - Q[x];
+        PQ2 = fma(d, d, PQ2);
+        W[x] = (zeta * P[x] + eta * Q[x]) * isum;
+      }
+      double F[kBoysMaxM + 1];
+      boys_eval(p.ltot, rho * PQ2, B.boys, F);
+      const double pre = B.pp_pref[ia] * B.pp_pref[ic] * sqrt(isum);
+      Real *e = ptab + lane * stride;
+      for (int m = 0; m <= p.ltot; ++m) e[m] = Real(pre * F[m]);
+      Real *cf = e + p.ltot + 1;
+      for (int x = 0; x < 3; ++x) {
+        cf[kPAx + x] = Real(P[x] - A[x]);
+        cf[kQCx + x] = Real(Q[x] - C[x]);
+        cf[kWPx + x] = Real(W[x] - P[x]);
+        cf[kWQx + x] = Real(W[x] - Q[x]);
+      }
+      cf[kHalfZeta] = Real(0.5 * izeta);
+      cf[kHalfEta] = Real(0.5 * ieta);
+      cf[kRhoZeta] = Real(rho * izeta);
+      cf[kRhoEta] = Real(rho * ieta);
+      cf[kHalfSum] = Real(0.5 * isum);
+      cf[kWA] = Real(2.0 * B.pp_a[ia]);
+      cf[kWB] = Real(2.0 * B.pp_b[ia]);
+      cf[kWC] = Real(2.0 * B.pp_a[ic]);
+      Real *h = cf + kNumCoef;
+      for (int n = 0; n < kNmax; ++n) {
+        h[n] = Real(0.5 * n * izeta);
+        h[kNmax + n] = Real(0.5 * n * ieta);
+        h[2 * kNmax + n] = Real(0.5 * n * isum);
+      }
+    }
+    __syncwarp();
+    // stage 2: recurrences, G primitive quartets at a time
+    const int nchunk = min(32, npq - c0);
+    for (int r0 = 0; r0 < nchunk; r0 += G) {
+      const int loc = r0 + g;
+      const bool active = loc < nchunk;
+      const Real *e = ptab + loc * stride;
+      const Real *cf = e + p.ltot + 1;
+      const Real *h = cf + kNumCoef;
+      if (active) {
+        for (int t = s; t <= p.ltot + 1; t += S) my_vrr[t] = t == 0 ? Real(0) : e[t - 1];
+      }
+      __syncwarp();
+      for (int L = 0; L < p.nvrr_level; ++L) {
+        const int i0 = PR.levels[p.vrr_level0 + L], i1 = PR.levels[p.vrr_level0 + L + 1];
+        if (active) {
+          for (int k = i0 + s; k < i1; k += S) {
+            const VrrInstr in = PR.vrr[k];
+            const int kd = in.kind, d = in.dir;
+            Real t = cf[kPAx + 3 * kd + d] * my_vrr[in.s0];
+            t = fma(cf[kWPx + 3 * kd + d], my_vrr[in.s1], t);
+            Real u = fma(-cf[kRhoZeta + kd], my_vrr[in.s3], my_vrr[in.s2]);
+            t = fma(h[kd * kNmax + in.n1], u, t);
+            t = fma(h[2 * kNmax + in.n2], my_vrr[in.s4], t);
+            my_vrr[in.tgt] = t;
+          }
+        }
+        __syncwarp();
+      }
+      if (active) {
+        for (int k = p.acc_begin + s; k < p.acc_begin + p.nacc; k += S) {
+          const AccInstr a = PR.acc[k];
+          Real w = a.chan == 0 ? Real(1) : cf[kWA + a.chan - 1];
+          my_acc[a.acc] = fma(w, my_vrr[a.slot], my_acc[a.acc]);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // reduce the group accumulators into group 0's
+  if (G > 1) {
+    for (int t = lane; t < p.acc_total; t += 32) {
+      Real v = acc0[t];
+      for (int gg = 1; gg < G; ++gg) v += accs[(G - 1 - gg) * p.acc_total + t];
+      acc0[t] = v;
+    }
+  }
+  __syncwarp();
+  return acc0;
+}
+
+// Horizontal recurrence of one output tile on the contracted accumulators acc0
+// (followed in memory by the work region); returns the tile's output block.
+template <typename Real>
+__device__ Real *hrr_tile(const DevBasis &B, const DevProgs &PR, const ClassProg &p, int tile,
+                          Real *acc0, int ip, int jp, int lane) {
+  const TileProg T = PR.tiles[p.tile_begin + tile];
+  const int2 sab = B.pair_sh[ip], scd = B.pair_sh[jp];
+  const double *A = B.sh_ctr + 3 * sab.x, *Bc = B.sh_ctr + 3 * sab.y;
+  const double *C = B.sh_ctr + 3 * scd.x, *Dc = B.sh_ctr + 3 * scd.y;
+  if (lane == 0) acc0[p.acc_total] = Real(0);  // zero slot
+  __syncwarp();
+  Real X[2][3];
+  for (int x = 0; x < 3; ++x) {
+    X[0][x] = Real(A[x] - Bc[x]);
+    X[1][x] = Real(C[x] - Dc[x]);
+  }
+  for (int L = 0; L < T.nhrr_level; ++L) {
+    const int i0 = PR.levels[T.hrr_level0 + L], i1 = PR.levels[T.hrr_level0 + L + 1];
+    for (int k = i0 + lane; k < i1; k += 32) {
+      const HrrInstr in = PR.hrr[k];
+      Real coef = in.kind < 2 ? X[in.kind][in.dir] : -Real(in.dir);
+      acc0[in.tgt] = fma(coef, acc0[in.s1], acc0[in.s0]);
+    }
+    __syncwarp();
+  }
+  return acc0 + T.out_base;
+}
+
+// Index sets of the ten digestion placements (Eq. quartet_scatter with every
+// permutational image of the unique quartet applied, non-symmetric D):
+// out(row,col) += w * sum_{u,v} I * M(row2, col2); indices 0..3 = a, b, c, d.
+struct Placement {
+  int orow, ocol, srow, scol, isJ;
+};
+__constant__ Placement c_place[10] = {
+    {0, 1, 2, 3, 1}, {2, 3, 0, 1, 1},  // J half: Jh[ab] += I S[cd], Jh[cd] += I S[ab]
+    {0, 2, 1, 3, 0}, {1, 2, 0, 3, 0}, {0, 3, 1, 2, 0}, {1, 3, 0, 2, 0},
+    {2, 0, 3, 1, 0}, {3, 0, 2, 1, 0}, {2, 1, 3, 0, 0}, {3, 1, 2, 0, 0}};
+
+template <typename Real>
+__device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], const int n[4],
+                          double w, int N, int lane) {
+  const int str[4] = {n[1] * n[2] * n[3], n[2] * n[3], n[3], 1};
+  const int nd = a.nd;
+  for (int pl = 0; pl < 10; ++pl) {
+    const Placement P = c_place[pl];
+    if (P.isJ ? a.J == nullptr : a.K == nullptr) continue;
+    const double *M = P.isJ ? a.S : a.D;
+    double *T = P.isJ ? a.J : a.K;
+    const int nr = n[P.orow], nc = n[P.ocol], nu = n[P.srow], nv = n[P.scol];
+    const int sr = str[P.orow], sc = str[P.ocol], su = str[P.srow], sv = str[P.scol];
+    const int items = nr * nc * nd;
+    for (int t = lane; t < items; t += 32) {
+      const int q = t % nd, o = t / nd;
+      const int x = o / nc, y = o % nc;
+      const Real *Ib = I + x * sr + y * sc;
+      const double *Mb = M + ((size_t)off[P.srow] * N + off[P.scol]) * nd + q;
+      Real acc = Real(0);
+      for (int u = 0; u < nu; ++u)
+        for (int v = 0; v < nv; ++v)
+          acc = fma(Ib[u * su + v * sv], Real(__ldg(Mb + ((size_t)u * N + v) * nd)), acc);
+      atomicAdd(T + ((size_t)(off[P.orow] + x) * N + off[P.ocol] + y) * nd + q, w * (double)acc);
+    }
+  }
+}
+
+// Gamma of one quartet for the gradient: the sum over the distinct images of
+// G_{mu nu ka rho} = sum_r [cJ P_r[mu][nu] Q_r[ka][rho] + cK P_r[mu][ka] Q_r[nu][rho]]
+// (Eq. jkderiv), times the degeneracy weight w, into gam[ijkl].
+__device__ void gamma_block(const JKArgs &a, double *gam, const int off[4], const int n[4],
+                            double w, int N, int lane) {
+  const int nq = n[0] * n[1] * n[2] * n[3];
+  const int nt = a.nd;
+  for (int e = lane; e < nq; e += 32) {
+    const int l = e % n[3], k = (e / n[3]) % n[2], j = (e / (n[3] * n[2])) % n[1],
+              i = e / (n[3] * n[2] * n[1]);
+    const size_t mu = off[0] + i, nu = off[1] + j, ka = off[2] + k, rho = off[3] + l;
+    double g = 0.0;
+    for (int r = 0; r < nt; ++r) {
+      const double *P = a.P + r, *Q = a.Q + r;
+#define PX(x, y) __ldg(P + ((x) * N + (y)) * nt)
+#define QX(x, y) __ldg(Q + ((x) * N + (y)) * nt)
+      const double gJ = (PX(mu, nu) + PX(nu, mu)) * (QX(ka, rho) + QX(rho, ka)) +
+                        (PX(ka, rho) + PX(rho, ka)) * (QX(mu, nu) + QX(nu, mu));
+      const double gK = PX(mu, ka) * QX(nu, rho) + PX(nu, ka) * QX(mu, rho) +
+                        PX(mu, rho) * QX(nu, ka) + PX(nu, rho) * QX(mu, ka) +
+                        PX(ka, mu) * QX(rho, nu) + PX(rho, mu) * QX(ka, nu) +
+                        PX(ka, nu) * QX(rho, mu) + PX(rho, nu) * QX(ka, mu);
+#undef PX
+#undef QX
+      g = fma(a.cJ, gJ, fma(a.cK, gK, g));
+    }
+    gam[e] = w * g;
+  }
+}
+
+// ------------------------------------------------------------- the kernel
+// One warp per work item (bra pair, ket range); warps of a CTA are independent.
+template <typename Real, int MODE>
+__global__ void __launch_bounds__(128) quartet_kernel(DevBasis B, DevProgs PR, ClassLaunch CL,
+                                                      const WorkItem *__restrict__ items, int nitems,
+                                                      int ket_base, JKArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const ClassProg &p = CL.p;
+  unsigned char *wbase = smem_raw + (size_t)warp * CL.smem_per_warp;
+  Real *sm = reinterpret_cast<Real *>(wbase);
+  double *gam = reinterpret_cast<double *>(wbase + gamma_offset(p, CL.G, sizeof(Real)));
+  const int N = B.nao;
+  for (int it = blockIdx.x * CL.warps + warp; it < nitems; it += gridDim.x * CL.warps) {
+    const WorkItem W = items[it];
+    const int2 sab = B.pair_sh[W.bra];
+    for (int kk = 0; kk < W.nk; ++kk) {
+      const int jp = ket_base + W.k0 + kk;
+      const int2 scd = B.pair_sh[jp];
+      Real *acc0 = quartet_block<Real>(B, PR, p, CL.G, sm, W.bra, jp, lane);
+      const int sh[4] = {sab.x, sab.y, scd.x, scd.y};
+      int off[4], n[4];
+      for (int t = 0; t < 4; ++t) {
+        off[t] = B.sh_ao[sh[t]];
+        n[t] = ncart(B.sh_l[sh[t]]);
+      }
+      double w = 1.0;
+      if (sab.x == sab.y) w *= 0.5;
+      if (scd.x == scd.y) w *= 0.5;
+      if (W.bra == jp) w *= 0.5;
+      if (MODE == kGrad) gamma_block(a, gam, off, n, w, N, lane);
+      double g9 = 0.0;  // lane t < 9 keeps component t
+      for (int tile = 0; tile < p.ntile; ++tile) {
+        const Real *I = hrr_tile<Real>(B, PR, p, tile, acc0, W.bra, jp, lane);
+        if (MODE == kStore) {
+          double *o = a.out + a.out_off[it] + ((long long)kk * p.ntile + tile) * p.nout;
+          for (int t = lane; t < p.nout; t += 32) o[t] = (double)I[t];
+        } else if (MODE == kJK) {
+          digest_jk<Real>(a, I, off, n, w, N, lane);
+        } else {
+          double v = 0.0;
+          for (int e = lane; e < p.nout; e += 32) v = fma((double)I[e], gam[e], v);
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == tile) g9 = v;
+        }
+        __syncwarp();
+      }
+      if (MODE == kGrad) {
+        // lanes 0..8 hold dE/dX for X = A_x..C_z; centre D by translational invariance
+        const int x = lane % 3;
+        const double gA = __shfl_sync(0xffffffffu, g9, x), gB = __shfl_sync(0xffffffffu, g9, 3 + x),
+                     gC = __shfl_sync(0xffffffffu, g9, 6 + x);
+        if (lane < 3) {
+          atomicAdd(a.grad + 3 * B.sh_atom[sh[0]] + x, gA);
+          atomicAdd(a.grad + 3 * B.sh_atom[sh[1]] + x, gB);
+          atomicAdd(a.grad + 3 * B.sh_atom[sh[2]] + x, gC);
+          atomicAdd(a.grad + 3 * B.sh_atom[sh[3]] + x, -(gA + gB + gC));
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// --------------------------------------------------------- layout kernels
+// [nd][N][N] -> q-innermost [(mu*N+nu)*nd + q]; optionally also S = D + D^T.
+__global__ void to_qinner(const double *__restrict__ D, double *__restrict__ Dq,
+                          double *__restrict__ Sq, int nd, int N) {
+  const size_t NN = (size_t)N * N;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < NN * nd;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t % nd);
+    const size_t mn = t / nd;
+    const int mu = (int)(mn / N), nu = (int)(mn % N);
+    const double v = D[q * NN + mn];
+    Dq[t] = v;
+    if (Sq) Sq[t] = v + D[q * NN + (size_t)nu * N + mu];
+  }
+}
+
+// J[q] = Jh[q] + Jh[q]^T and K[q] from the q-innermost accumulators.
+__global__ void from_qinner(const double *__restrict__ Jq, const double *__restrict__ Kq,
+                            double *__restrict__ J, double *__restrict__ K, int nd, int N) {
+  const size_t NN = (size_t)N * N;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < NN * nd;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t / NN);
+    const size_t mn = t % NN;
+    const int mu = (int)(mn / N), nu = (int)(mn % N);
+    if (J) J[t] = Jq[mn * nd + q] + Jq[((size_t)nu * N + mu) * nd + q];
+    if (K) K[t] = Kq[mn * nd + q];
+  }
+}
+
+// ----------------------------------------------------- pseudo-densities
+// Y[q*npair+p][i][a] = exp(t_q (eps_i - eps_a)) X[p][i][a]
+__global__ void scale_amplitudes(const double *__restrict__ X, const double *__restrict__ eo,
+                                 const double *__restrict__ ev, const double *__restrict__ t,
+                                 double *__restrict__ Y, int nlap, int npair, int no, int nv) {
+  const size_t per = (size_t)no * nv, total = per * npair * nlap;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const size_t qp = k / per, ia = k % per;
+    const int q = (int)(qp / npair), p = (int)(qp % npair);
+    const int i = (int)(ia / nv), aa = (int)(ia % nv);
+    Y[k] = exp(t[q] * (eo[i] - ev[aa])) * X[(size_t)p * per + ia];
+  }
+}
+
+// Batched FP64 GEMM with 16x16 tiles, C[b][m][n] = sum_k A(b)[m][k] Bop(b)[k][n],
+// Bop[k][n] = B[n][k] when TRANSB else B[k][n].  Row-major, leading dims lda/ldb/ldc.
+template <bool TRANSB>
+__global__ void gemm_f64(const double *__restrict__ A, long long strideA,
+                         const double *__restrict__ Bm, long long strideB, double *__restrict__ C,
+                         long long strideC, int M, int Nn, int Kd, int lda, int ldb, int ldc) {
+  __shared__ double As[16][17], Bs[16][17];  // As[m][k], Bs[k][n]
+  const int b = blockIdx.z;
+  const double *Ab = A + b * strideA, *Bb = Bm + b * strideB;
+  double *Cb = C + b * strideC;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int m0 = blockIdx.y * 16, n0 = blockIdx.x * 16;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < Kd; k0 += 16) {
+    As[ty][tx] = (m0 + ty < M && k0 + tx < Kd) ? Ab[(size_t)(m0 + ty) * lda + k0 + tx] : 0.0;
+    if (TRANSB)  // thread (tx,ty) reads B[n0+ty][k0+tx] (coalesced in tx) -> Bs[k=tx][n=ty]
+      Bs[tx][ty] = (n0 + ty < Nn && k0 + tx < Kd) ? Bb[(size_t)(n0 + ty) * ldb + k0 + tx] : 0.0;
+    else         // thread (tx,ty) reads B[k0+ty][n0+tx] -> Bs[k=ty][n=tx]
+      Bs[ty][tx] = (k0 + ty < Kd && n0 + tx < Nn) ? Bb[(size_t)(k0 + ty) * ldb + n0 + tx] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc = fma(As[ty][k], Bs[k][tx], acc);
+    __syncthreads();
+  }
+  if (m0 + ty < M && n0 + tx < Nn) Cb[(size_t)(m0 + ty) * ldc + n0 + tx] = acc;
+}
+
+}  // namespace ltjk

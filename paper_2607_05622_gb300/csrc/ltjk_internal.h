@@ -1,0 +1,113 @@
+// Internal structures shared by the host code and the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ltjk.h"
+
+namespace ltjk {
+
+constexpr int kMaxL = LTJK_MAX_L;      // value build: s, p, d
+constexpr int kMaxLDeriv = kMaxL + 1;  // one raise for the derivative integrals
+constexpr int kMaxPrim = 8;
+constexpr int kMaxPrimPair = kMaxPrim * kMaxPrim;
+constexpr int kBoysMaxM = 4 * kMaxLDeriv + 2;
+
+#ifdef __CUDACC__
+#define LTJK_HD __host__ __device__
+#else
+#define LTJK_HD
+#endif
+
+LTJK_HD inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+
+// Coefficient slots of one primitive quartet, stored after its base values
+// [00|00]^(m), m = 0..ltot, in the per-warp primitive table.
+enum CoefSlot {
+  kPAx = 0, kPAy, kPAz,   // bra step, first coefficient (P - A)
+  kQCx, kQCy, kQCz,       // ket step, first coefficient (Q - C)
+  kWPx, kWPy, kWPz,       // bra step, second coefficient (W - P)
+  kWQx, kWQy, kWQz,       // ket step, second coefficient (W - Q)
+  kHalfZeta,              // 1/(2 zeta)
+  kHalfEta,               // 1/(2 eta)
+  kRhoZeta,               // rho/zeta
+  kRhoEta,                // rho/eta
+  kHalfSum,               // 1/(2 (zeta+eta))
+  kWA,                    // derivative channel weights: 2 alpha, 2 beta, 2 gamma
+  kWB,
+  kWC,
+  kNumCoef
+};
+
+// One Obara-Saika step.  kind 0 (bra): raise e along dir
+//   t = PA*s0 + WP*s1 + n1/(2zeta) (s2 - rho/zeta s3)
+// kind 1 (ket): raise f along dir
+//   t = QC*s0 + WQ*s1 + n1/(2eta) (s2 - rho/eta s3) + n2/(2(zeta+eta)) s4
+struct VrrInstr {
+  uint16_t tgt, s0, s1, s2, s3, s4;
+  uint8_t kind, dir, n1, n2;
+};
+static_assert(sizeof(VrrInstr) == 16, "VrrInstr layout");
+
+// One horizontal step t = s0 + X_dir * s1, X = A - B (kind 0) or C - D (kind 1).
+struct HrrInstr {
+  uint16_t tgt, s0, s1;
+  uint8_t kind, dir;
+};
+static_assert(sizeof(HrrInstr) == 8, "HrrInstr layout");
+
+// Accumulation of one VRR target into a contracted accumulator:
+// acc[chan*acc_chan + acc] += weight(chan) * vrr[slot].
+struct AccInstr {
+  uint16_t slot, acc;
+  uint8_t chan, pad0;
+  uint16_t pad1;
+};
+static_assert(sizeof(AccInstr) == 8, "AccInstr layout");
+
+// One output tile of a class program: HRR levels and the contiguous output block.
+struct TileProg {
+  int hrr_level0, nhrr_level;  // level ranges in ProgramSet::levels
+  int out_base;                // HRR slot of output 0 (outputs contiguous)
+  int nout;                    // outputs of the tile (na nb nc nd)
+  int hrr_size;                // HRR slots beyond the accumulators this tile uses
+};
+
+// Device view of one class program (offsets into the shared instruction pools).
+struct ClassProg {
+  int la, lb, lc, ld, ltot;  // ltot includes the derivative raise when deriv
+  int deriv;                 // 0: plain integrals; 1: derivative channels
+  int nchan;                 // accumulator channels (1 plain, 4 deriv)
+  int vrr_begin, nvrr_level;  // level ranges are in level_pool[vrr_level0 .. +nvrr_level]
+  int vrr_level0;
+  int acc_begin, nacc;
+  int ntile, tile_begin;     // output tiles (1 plain; 9 = centre A,B,C x xyz for deriv)
+  int vrr_size;   // slots of one VRR region (slot 0 = zero, 1..ltot+1 = base values)
+  int acc_size;   // slots of one accumulator channel
+  int hrr_size;   // HRR slots beyond the accumulators, max over tiles (slot acc_total = zero)
+  int acc_total;  // nchan * acc_size
+  int nout;       // outputs per tile (na nb nc nd)
+  double vrr_flops, hrr_flops;  // flop model: per primitive quartet / per contracted quartet
+};
+
+struct ProgramSet {
+  std::vector<VrrInstr> vrr;
+  std::vector<HrrInstr> hrr;
+  std::vector<AccInstr> acc;
+  std::vector<int> levels;        // level boundaries (instruction index), per program
+  std::vector<TileProg> tiles;
+  std::vector<ClassProg> progs;   // index = class_index(la,lb,lc,ld,deriv)
+};
+
+// Class index of (la,lb,lc,ld) with la>=lb, lc>=ld (any bra/ket order).
+inline int pair_class(int la, int lb) { return la * (la + 1) / 2 + lb; }
+constexpr int kNumPairClass = (kMaxL + 1) * (kMaxL + 2) / 2;
+inline int quartet_index(int la, int lb, int lc, int ld, int deriv) {
+  return (deriv * kNumPairClass + pair_class(la, lb)) * kNumPairClass + pair_class(lc, ld);
+}
+
+void build_programs(ProgramSet &ps);
+void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv, ClassProg &out);
+
+}  // namespace ltjk

@@ -1,0 +1,259 @@
+"""Python binding of the C ABI in include/ltjk.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/libltjk.so``; PyTorch is
+used for device memory and streams.  There is no fallback: if the library is
+missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libltjk.so")
+
+OK, EINVAL, ENOMEM, EBUDGET, EUNSUPPORTED, ECUDA, ETIMEDOUT, ECANCELLED, ENOTREADY = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+FP64, MIXED = 0, 1
+MAX_L = 2
+
+
+class LtjkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ltjk error {code}: {msg}")
+        self.code = code
+
+
+class _Basis(ctypes.Structure):
+    _fields_ = [("natoms", ctypes.c_int), ("coords_host", ctypes.c_void_p),
+                ("nshells", ctypes.c_int), ("shell_atom_host", ctypes.c_void_p),
+                ("shell_l_host", ctypes.c_void_p), ("shell_nprim_host", ctypes.c_void_p),
+                ("exps_host", ctypes.c_void_p), ("coefs_host", ctypes.c_void_p)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("schwarz_tau", ctypes.c_double), ("mixed_tau", ctypes.c_double),
+                ("precision", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class CtxStats(ctypes.Structure):
+    _fields_ = [("nao", ctypes.c_int), ("nshells", ctypes.c_int), ("npairs", ctypes.c_int),
+                ("quartets_total", ctypes.c_int64), ("quartets_kept", ctypes.c_int64),
+                ("quartets_fp64", ctypes.c_int64), ("prim_quartets_kept", ctypes.c_int64),
+                ("cart_integrals_kept", ctypes.c_int64), ("eri_flops_per_build", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+# exported symbols and their signatures (restype int unless noted)
+_P, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+SIGNATURES = {
+    "ltjk_last_error": ([], ctypes.c_char_p),
+    "ltjk_version": ([], _I),
+    "ltjk_context_create": ([_P, _P, _P], _I),
+    "ltjk_context_destroy": ([_P], _I),
+    "ltjk_nao": ([_P, _P], _I),
+    "ltjk_context_stats": ([_P, _P], _I),
+    "ltjk_schwarz": ([_P, _P], _I),
+    "ltjk_laplace_quadrature": ([_D, _D, _I, _P, _P, _P], _I),
+    "ltjk_pseudo_densities": ([_P, _I, _I, _P, _P, _P, _P, _I, _P, _I, _P, _P, _P], _I),
+    "ltjk_jk_build": ([_P, _I, _P, _P, _P, _P], _I),
+    "ltjk_jk_grad": ([_P, _I, _P, _P, _D, _D, _P, _P], _I),
+    "ltjk_shell_quartets": ([_P, _I, _P, _I, _P, _P], _I),
+}
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} missing "
+                               "(run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        msg = lib().ltjk_last_error()
+        raise LtjkError(rc, msg.decode() if msg else "")
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, shape=None, name="tensor"):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+        raise ValueError(f"{name} must be a CUDA float64 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def laplace_quadrature(xmin: float, xmax: float, n: int):
+    """(t, w, max_rel_err) of the least-squares exponential sum for 1/x (Eq. laplace)."""
+    t = np.zeros(n)
+    w = np.zeros(n)
+    err = ctypes.c_double(0.0)
+    _check(lib().ltjk_laplace_quadrature(float(xmin), float(xmax), int(n),
+                                         t.ctypes.data_as(_P), w.ctypes.data_as(_P),
+                                         ctypes.byref(err)))
+    return t, w, err.value
+
+
+class Context:
+    """A molecule on the GPU: shell pairs, Schwarz factors and screened work lists."""
+
+    def __init__(self, mol, schwarz_tau=1e-12, mixed_tau=1e-6, precision=FP64, device=0):
+        self._keep = [np.ascontiguousarray(mol.coords, dtype=np.float64),
+                      np.ascontiguousarray(mol.shell_atom, dtype=np.int32),
+                      np.ascontiguousarray(mol.shell_l, dtype=np.int32),
+                      np.ascontiguousarray(mol.shell_nprim, dtype=np.int32),
+                      np.ascontiguousarray(mol.exps, dtype=np.float64),
+                      np.ascontiguousarray(mol.coefs, dtype=np.float64)]
+        c, a, l, n, e, k = self._keep
+        b = _Basis(c.shape[0], c.ctypes.data, l.shape[0], a.ctypes.data, l.ctypes.data,
+                   n.ctypes.data, e.ctypes.data, k.ctypes.data)
+        o = _Opts(float(schwarz_tau), float(mixed_tau), int(precision), int(device))
+        h = ctypes.c_void_p()
+        torch.cuda.set_device(device)
+        _check(lib().ltjk_context_create(ctypes.byref(b), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.device = device
+        self.natoms = c.shape[0]
+        self.nshells = l.shape[0]
+        nao = ctypes.c_int()
+        _check(lib().ltjk_nao(h, ctypes.byref(nao)))
+        self.nao = nao.value
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ltjk_context_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = CtxStats()
+        _check(lib().ltjk_context_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def schwarz(self) -> np.ndarray:
+        Q = np.zeros((self.nshells, self.nshells))
+        _check(lib().ltjk_schwarz(self._h, Q.ctypes.data_as(_P)))
+        return Q
+
+    def jk_build(self, D: torch.Tensor, J=None, K=None, want_j=True, want_k=True, stream=None):
+        nd, N = D.shape[0], self.nao
+        dp = _dev(D, (nd, N, N), "D")
+        if want_j and J is None:
+            J = torch.empty_like(D)
+        if want_k and K is None:
+            K = torch.empty_like(D)
+        jp = _dev(J, (nd, N, N), "J") if want_j else None
+        kp = _dev(K, (nd, N, N), "K") if want_k else None
+        _check(lib().ltjk_jk_build(self._h, nd, dp, jp, kp, _stream(stream)))
+        return J, K
+
+    def jk_grad(self, P: torch.Tensor, Q: torch.Tensor, cJ=1.0, cK=0.0, grad=None, stream=None):
+        nt, N = P.shape[0], self.nao
+        pp = _dev(P, (nt, N, N), "P")
+        qp = _dev(Q, (nt, N, N), "Q")
+        if grad is None:
+            grad = torch.empty((self.natoms, 3), dtype=torch.float64, device=P.device)
+        gp = _dev(grad, (self.natoms, 3), "grad")
+        _check(lib().ltjk_jk_grad(self._h, nt, pp, qp, float(cJ), float(cK), gp, _stream(stream)))
+        return grad
+
+    def pseudo_densities(self, C_occ, C_vir, eps_occ, eps_vir, X, t, D=None, stream=None):
+        N = self.nao
+        no, nv = C_occ.shape[1], C_vir.shape[1]
+        npair = X.shape[0]
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        nlap = t.shape[0]
+        if D is None:
+            D = torch.empty((nlap * npair, N, N), dtype=torch.float64, device=C_occ.device)
+        _check(lib().ltjk_pseudo_densities(
+            self._h, no, nv, _dev(C_occ, (N, no), "C_occ"), _dev(C_vir, (N, nv), "C_vir"),
+            _dev(eps_occ, (no,), "eps_occ"), _dev(eps_vir, (nv,), "eps_vir"), npair,
+            _dev(X, (npair, no, nv), "X"), nlap, t.ctypes.data_as(_P),
+            _dev(D, (nlap * npair, N, N), "D"), _stream(stream)))
+        return D
+
+    def shell_quartets(self, quartets, precision=FP64, stream=None):
+        """Contracted blocks of (a b|c d) for each (a,b,c,d) in canonical pair order."""
+        q = np.ascontiguousarray(np.asarray(quartets, dtype=np.int32).reshape(-1, 4))
+        sizes = []
+        ls = self._keep[2]
+        for a, b, c, d in q:
+            sizes.append(int(np.prod([(int(ls[s]) + 1) * (int(ls[s]) + 2) // 2 for s in (a, b, c, d)])))
+        out = torch.zeros(max(sum(sizes), 1), dtype=torch.float64, device=f"cuda:{self.device}")
+        _check(lib().ltjk_shell_quartets(self._h, q.shape[0], q.ctypes.data_as(_P), int(precision),
+                                         _dev(out, None, "out"), _stream(stream)))
+        torch.cuda.current_stream().synchronize()
+        res, off = [], 0
+        host = out.cpu().numpy()
+        for (a, b, c, d), n in zip(q, sizes):
+            shp = [(int(ls[s]) + 1) * (int(ls[s]) + 2) // 2 for s in (a, b, c, d)]
+            res.append(host[off:off + n].reshape(shp))
+            off += n
+        return res
+
+
+class JKEnergy(torch.autograd.Function):
+    """E = sum_r <P_r, cJ J[Q_r] + cK K[Q_r]> = sum_r [cJ J(P_r,Q_r) + cK K(P_r,Q_r)].
+
+    forward(coords, P, Q, mol, cJ, cK, opts) builds a context at ``coords``;
+    backward gives dE/dcoords from ltjk_jk_grad (Eq. jkderiv) and
+    dE/dP_r = cJ J[Q_r] + cK K[Q_r], dE/dQ_r = cJ J[P_r] + cK K[P_r] from
+    ltjk_jk_build (the adjoint of a J/K build is a J/K build)."""
+
+    @staticmethod
+    def forward(ctx_, coords, P, Q, mol, cJ=1.0, cK=0.0, opts=None):
+        opts = dict(opts or {})
+        m = mol.with_coords(coords.detach().cpu().numpy().astype(np.float64))
+        c = Context(m, **opts)
+        J, K = c.jk_build(Q.detach().contiguous())
+        F = cJ * J + cK * K
+        E = torch.sum(P.detach() * F)
+        ctx_.save_for_backward(P, Q, F)
+        ctx_.c = c
+        ctx_.cJ, ctx_.cK = cJ, cK
+        return E
+
+    @staticmethod
+    def backward(ctx_, gE):
+        P, Q, F = ctx_.saved_tensors
+        c = ctx_.c
+        gc = gP = gQ = None
+        if ctx_.needs_input_grad[0]:
+            gc = c.jk_grad(P.detach().contiguous(), Q.detach().contiguous(), ctx_.cJ, ctx_.cK) * gE
+            gc = gc.to(P.device)
+        if ctx_.needs_input_grad[1]:
+            gP = F * gE
+        if ctx_.needs_input_grad[2]:
+            J, K = c.jk_build(P.detach().contiguous())
+            gQ = (ctx_.cJ * J + ctx_.cK * K) * gE
+        return gc, gP, gQ, None, None, None, None
