@@ -1,0 +1,357 @@
+"""Benchmark of the Laplace-transform AO-direct J/K hot path on GB300.
+
+One step = one Laplace J/K request on the 200-AO chain (10 heavy 3s2p1d + 10 H
+2s1p, 35 occupied, 3 transition pairs x 16 Laplace points = 48 non-symmetric
+densities, Schwarz 1e-12): Laplace quadrature (host, cached per range), the
+pseudo-densities D_q on the device, and J[D_q], K[D_q] with ERIs recomputed on
+the fly.  The context (shell pairs, Schwarz factors, work lists) is built once
+per geometry and reused, as a resident per-molecule cache.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2607_05622_gb300 import workloads as W  # noqa: E402
+
+HBM_L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# FP64 / FP32 FMA peaks from unit counts and clocks: 152 SMs; per SM per clock
+# 128 FP32 FMA lanes and 2 FP64 FMA (the nominal 1.25 TFLOP/s FP64 at 2.07 GHz).
+def alu_peaks(sm_mhz):
+    f = sm_mhz * 1e6
+    return {"fp32_tflops": 152 * 128 * 2 * f / 1e12, "fp64_tflops": 152 * 2 * 2 * f / 1e12}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self, device_index=0):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [l.strip().split(", ") for l in open(self.path) if l.strip()]
+        except Exception:
+            return out
+        rows = [r for r in rows if len(r) >= 9 and r[0] == str(device_index)]
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("LTJK_BENCH_GLOO") is None else "gloo")
+    return world, rank, local
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_oracle_sample(w, budget_s=20.0, nblocks=None):
+    """Time the oracle (as it stands) on a bounded sample of the workload: J and K
+    blocks of randomly chosen shell pairs for all densities, each block summing
+    over every ordered ket (J) or (b,d) (K) shell pair of the full molecule,
+    unscreened.  The full build is extrapolated by shell-quartet evaluations."""
+    from oracle import oracle as O
+    O.build()
+    mol = w.mol
+    ns = mol.nshells
+    nd = w.ndens
+    rng = np.random.default_rng(0)
+    D = rng.standard_normal((nd, mol.nao, mol.nao))
+    t0 = time.perf_counter()
+    evals = 0
+    done = 0
+    while True:
+        a, b = int(rng.integers(ns)), int(rng.integers(ns))
+        O.j_block(mol, D, a, b)
+        O.k_block(mol, D, a, b)
+        evals += 2 * ns * ns
+        done += 1
+        el = time.perf_counter() - t0
+        if (nblocks and done >= nblocks) or (not nblocks and el > budget_s):
+            break
+    el = time.perf_counter() - t0
+    rate = evals / el  # shell quartets (with all densities) per second
+    unique = ns * (ns + 1) // 2
+    unique = unique * (unique + 1) // 2
+    build_s = unique / rate
+    return {"value": nd / build_s, "unit": "builds/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{done} J+K shell-pair blocks x {nd} densities ({evals} ordered shell "
+                      f"quartets in {el:.1f} s), extrapolated to {unique} unique quartets, unscreened",
+            "seconds": el}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    w = W.config2()
+    cb = None
+    times = []
+    for step in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(w, nblocks=2)
+        if step >= args.warmup:
+            times.append(r["seconds"])
+            cb = r
+    vals = cb["value"]
+    line = {"impl": "reference", "metric": "Laplace J/K builds/s (200-AO chain, 48 densities)",
+            "value": vals, "unit": "builds/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": vals, "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU path
+def run_gpu(args, world, rank, local):
+    import torch
+    from paper_2607_05622_gb300 import ltjk
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    w = W.config2()
+    mol = w.mol
+    N, nd = mol.nao, w.ndens
+    prec = ltjk.MIXED if args.precision == "mixed" else ltjk.FP64
+    t0 = time.perf_counter()
+    ctx = ltjk.Context(mol, schwarz_tau=w.schwarz_tau, mixed_tau=1e-6, precision=prec, device=local)
+    setup_s = time.perf_counter() - t0
+    st = ctx.stats()
+    xmin = 2.0 * (w.eps_vir.min() - w.eps_occ.max())
+    xmax = 2.0 * (w.eps_vir.max() - w.eps_occ.min())
+    tq, wq, lap_err = ltjk.laplace_quadrature(xmin, xmax, w.nlap)
+    Co, Cv = torch.from_numpy(w.C_occ).to(dev), torch.from_numpy(w.C_vir).to(dev)
+    eo, ev = torch.from_numpy(w.eps_occ).to(dev), torch.from_numpy(w.eps_vir).to(dev)
+    X = torch.from_numpy(np.ascontiguousarray(w.X)).to(dev)
+    D = torch.empty((nd, N, N), dtype=torch.float64, device=dev)
+    J = torch.empty_like(D)
+    K = torch.empty_like(D)
+    flush = torch.empty(HBM_L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        t, _, _ = ltjk.laplace_quadrature(xmin, xmax, w.nlap)
+        ctx.pseudo_densities(Co, Cv, eo, ev, X, t, D=D)
+        ctx.jk_build(D, J, K)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # device-timed steps, L2 flushed between steps (outside the timed events)
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    l0 = ltjk.launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    with Clocks() as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev_s[i].record(stream)
+            t, _, _ = ltjk.laplace_quadrature(xmin, xmax, w.nlap)
+            ctx.pseudo_densities(Co, Cv, eo, ev, X, t, D=D)
+            ev_k0[i].record(stream)
+            ctx.jk_build(D, J, K)
+            ev_e[i].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = ltjk.launch_count() - l0
+    step_ms = [ev_s[i].elapsed_time(ev_e[i]) for i in range(args.steps)]
+    jk_ms = [ev_k0[i].elapsed_time(ev_e[i]) for i in range(args.steps)]
+    total_s = reduce_max(sum(step_ms) / 1e3, world)
+    value = world * nd * args.steps / total_s
+    # end to end: pinned host inputs -> device -> D -> J, K -> pinned host outputs
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    hC, hV, he, hv, hX = pin(w.C_occ), pin(w.C_vir), pin(w.eps_occ), pin(w.eps_vir), pin(w.X)
+    hJ = torch.empty((nd, N, N), dtype=torch.float64).pin_memory()
+    hK = torch.empty_like(hJ)
+    h2d = sum(x.numel() * 8 for x in (hC, hV, he, hv, hX))
+    d2h = 2 * nd * N * N * 8
+
+    def e2e_step():
+        t, _, _ = ltjk.laplace_quadrature(xmin, xmax, w.nlap)
+        dC, dV = hC.to(dev, non_blocking=True), hV.to(dev, non_blocking=True)
+        de, dv, dX = he.to(dev, non_blocking=True), hv.to(dev, non_blocking=True), hX.to(dev, non_blocking=True)
+        Dd = ctx.pseudo_densities(dC, dV, de, dv, dX, t)
+        Jd, Kd = ctx.jk_build(Dd)
+        hJ.copy_(Jd, non_blocking=True)
+        hK.copy_(Kd, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ne = max(2, min(args.steps, 5))
+    barrier(world)
+    torch.cuda.synchronize()
+    e_s.record(stream)
+    for _ in range(ne):
+        e2e_step()
+    e_e.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(e_s.elapsed_time(e_e) / 1e3, world)
+    e2e_val = world * nd * ne / e2e_s
+    # error of this precision against a plain FP64 build on the same GPU
+    err = {}
+    if prec == ltjk.MIXED:
+        c64 = ltjk.Context(mol, schwarz_tau=w.schwarz_tau, precision=ltjk.FP64, device=local)
+        J64, K64 = c64.jk_build(D)
+        torch.cuda.synchronize()
+        e64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e64[0].record(stream)
+        c64.jk_build(D, J64, K64)
+        e64[1].record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = e64[0].elapsed_time(e64[1])
+        dj = (J - J64).abs().max().item()
+        dk = (K - K64).abs().max().item()
+        err = {"vs": "plain FP64 build on the same GPU (itself parity-tested against the oracle)",
+               "J_max_abs": dj, "K_max_abs": dk,
+               "J_max_rel_to_max": dj / J64.abs().max().item(), "K_max_rel_to_max": dk / K64.abs().max().item(),
+               "fp64_single_request_builds_per_s": nd / (fp64_ms / 1e3)}
+        del c64
+    # roofline of the dominant kernel (the J/K quartet kernels of one build)
+    clocks = clk.summary(local)
+    sm_mhz = clocks["sm_mhz"] or 1965.0
+    jk_s = statistics.mean(jk_ms) / 1e3
+    dig = 20.0 * st["cart_integrals_kept"] * nd
+    flops = st["eri_flops_per_build"] + dig
+    pk = alu_peaks(2070.0)
+    peak = pk["fp64_tflops"] if prec == ltjk.FP64 else pk["fp32_tflops"]
+    roof = {"bound": "alu", "pipe": "fp64" if prec == ltjk.FP64 else "fp32 (bulk) + fp64 (Boys, promoted, accumulation)",
+            "achieved": flops / jk_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": flops / jk_s / 1e12 / peak, "traffic": None,
+            "algorithmic_flops_per_build": flops,
+            "peak_source": "unit counts x 2070 MHz max SM clock (152 SMs; 128 FP32 or 2 FP64 FMA/clk/SM)"}
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_oracle_sample(w, budget_s=args.cpu_seconds)
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    line = {
+        "metric": f"Laplace J/K builds/s ({args.precision}, 200-AO chain, 48 densities)",
+        "value": value, "unit": "builds/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == ltjk.FP64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "precision": args.precision, "schwarz_tau": w.schwarz_tau,
+                   "mixed_tau": 1e-6 if prec == ltjk.MIXED else None, "nao": N, "ndens": nd,
+                   "laplace_points": w.nlap, "laplace_max_rel_err": lap_err,
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "quartets_per_s": world * st["quartets_kept"] * args.steps / total_s,
+        "prim_quartets_per_s": world * st["prim_quartets_kept"] * args.steps / total_s,
+        "jk_build_ms": statistics.mean(jk_ms),
+        "setup_ms": 1e3 * setup_s,
+        "work": {k: st[k] for k in ("quartets_total", "quartets_kept", "quartets_fp64",
+                                    "prim_quartets_kept", "cart_integrals_kept", "eri_flops_per_build")},
+        "error_vs_fp64": err or None,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "builds/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

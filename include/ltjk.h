@@ -64,6 +64,10 @@ const char *ltjk_last_error(void);
 /* Library version, MAJOR*10000 + MINOR*100 + PATCH. */
 int ltjk_version(void);
 
+/* Number of CUDA kernels this library has launched in this process (all
+   devices, all contexts), for accounting.  Host-only. */
+int ltjk_launch_count(unsigned long long *count);
+
 /* --------------------------------------------------------------- contexts */
 /* A molecule in a Cartesian contracted Gaussian basis.  All arrays are host
    arrays and are copied by ltjk_context_create.
@@ -183,6 +187,64 @@ int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, do
    the build, in FP64 (precision = LTJK_FP64) or FP32 (LTJK_MIXED). */
 int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int precision,
                         double *out, ltjk_stream stream);
+
+/* --------------------------------------------------------------- serving */
+/* A continuous-batching solver service on one device.  A scheduler thread
+   admits submitted requests first-come-first-served whenever their device
+   scratch fits the HBM budget (one slab allocated at creation, first-fit with
+   adjacent-block coalescing), and advances every admitted request together in
+   steps: each step launches, per quartet class, one kernel over the next chunk
+   of work items of all active requests of that class, so requests that arrive
+   while others run share the device.  Each request completes on its own; its
+   result equals the stand-alone ltjk_jk_build / ltjk_jk_grad result up to the
+   order of floating-point additions.  Contexts (resident shell-pair data) are
+   owned by the caller and must outlive their requests; a context may serve
+   several concurrent requests.  Inputs must be complete on the device when
+   ltjk_service_submit is called; outputs are valid once ltjk_service_wait
+   returns LTJK_OK (or poll reports done with LTJK_OK). */
+typedef struct ltjk_service ltjk_service;
+
+#define LTJK_REQ_JK 0
+#define LTJK_REQ_GRAD 1
+
+typedef struct {
+  int kind;            /* LTJK_REQ_JK or LTJK_REQ_GRAD */
+  ltjk_ctx *ctx;       /* molecule and precision (caller-owned) */
+  int n;               /* densities (J/K) or terms (gradient), 1..4096 */
+  const double *D;     /* J/K: [n][N][N] device, read */
+  double *J, *K;       /* J/K: [n][N][N] device, written (either may be NULL) */
+  const double *P, *Q; /* gradient: [n][N][N] device, read */
+  double cJ, cK;       /* gradient coefficients (see ltjk_jk_grad) */
+  double *grad;        /* gradient: [natoms][3] device, written */
+} ltjk_request;
+
+typedef struct {
+  uint64_t submitted, completed, cancelled, failed;
+  double p50_ms, p99_ms, mean_ms;  /* latency submit -> completion, completed requests */
+  double throughput_rps;           /* completed / (last completion - first submission) */
+  size_t bytes_in_use, bytes_peak, budget;
+  uint64_t steps, launches;
+  int active, queued;
+} ltjk_svc_stats;
+
+/* Create a service with an HBM budget (bytes, >= 1 MiB, allocated now) on a device. */
+int ltjk_service_create(size_t hbm_budget_bytes, int device, ltjk_service **out);
+/* Queue a request; *ticket identifies it.  LTJK_EBUDGET if it can never fit. */
+int ltjk_service_submit(ltjk_service *svc, const ltjk_request *req, uint64_t *ticket);
+/* Non-blocking: *done = 1 once finished; then returns the request's status. */
+int ltjk_service_poll(ltjk_service *svc, uint64_t ticket, int *done);
+/* Wait at most timeout_s seconds: LTJK_OK, LTJK_ETIMEDOUT (request continues),
+   LTJK_ECANCELLED, or the request's failure code.  Never waits unboundedly. */
+int ltjk_service_wait(ltjk_service *svc, uint64_t ticket, double timeout_s);
+/* Cancel: a queued request is dropped; an active one stops issuing work and
+   releases its memory once its launched work has drained. */
+int ltjk_service_cancel(ltjk_service *svc, uint64_t ticket);
+int ltjk_service_stats(ltjk_service *svc, ltjk_svc_stats *out);
+/* Fault injection for tests: the next `count` admissions fail with LTJK_ENOMEM
+   as if the allocation had failed; other requests are unaffected. */
+int ltjk_service_fail_next_admission(ltjk_service *svc, int count);
+/* Cancel queued requests, drain active ones, stop the scheduler, free the slab. */
+int ltjk_service_destroy(ltjk_service *svc);
 
 #ifdef __cplusplus
 }

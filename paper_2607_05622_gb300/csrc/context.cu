@@ -2,6 +2,10 @@
 // Schwarz screening, work lists, the J/K build, the gradient adjoint, the
 // pseudo-densities and the inspection call.
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -22,6 +26,8 @@ using namespace ltjk;
   } while (0)
 
 namespace {
+
+std::atomic<unsigned long long> g_launches{0};  // kernels launched by this library
 
 constexpr int kKetChunk = 16;            // ket pairs per work item
 constexpr int kSmemBudget = 200 * 1024;  // bytes of shared memory per CTA we plan for
@@ -102,15 +108,24 @@ int device_programs(int dev, DevProgs *out, const double **boys) {
     if ((rc = v->upload(ps->vrr)) || (rc = h->upload(ps->hrr)) || (rc = a->upload(ps->acc)) ||
         (rc = l->upload(ps->levels)) || (rc = t->upload(ps->tiles)))
       return rc;
-    std::vector<double> tab((size_t)kBoysRows * kBoysCols);
-    boys_table(kBoysRows, kBoysCols, kBoysStep, tab.data());
+    // tab[k][m][j] = F_{m+j}(T_k) / j!
+    std::vector<double> raw((size_t)kBoysRows * kBoysRaw);
+    boys_table(kBoysRows, kBoysRaw, kBoysStep, raw.data());
+    std::vector<double> tab((size_t)kBoysRows * kBoysM * kBoysTaylor);
+    for (int k = 0; k < kBoysRows; ++k)
+      for (int m = 0; m < kBoysM; ++m) {
+        double fact = 1.0;
+        for (int j = 0; j < kBoysTaylor; ++j) {
+          if (j > 0) fact *= j;
+          tab[((size_t)k * kBoysM + m) * kBoysTaylor + j] = raw[(size_t)k * kBoysRaw + m + j] / fact;
+        }
+      }
     if ((rc = b->upload(tab))) return rc;
-    double inv_odd[kBoysCols + 2], inv_int[kBoysTaylor + 1];
-    for (int m = 0; m < kBoysCols + 2; ++m) inv_odd[m] = 1.0 / (2 * m + 1);
-    inv_int[0] = 0.0;
-    for (int j = 1; j <= kBoysTaylor; ++j) inv_int[j] = 1.0 / j;
+    double inv_odd[kBoysRaw + 2], half_n[2 * kMaxLDeriv + 4];
+    for (int m = 0; m < kBoysRaw + 2; ++m) inv_odd[m] = 1.0 / (2 * m + 1);
+    for (int n = 0; n < 2 * kMaxLDeriv + 4; ++n) half_n[n] = 0.5 * n;
     CUDA_TRY(cudaMemcpyToSymbol(c_inv_odd, inv_odd, sizeof(inv_odd)));
-    CUDA_TRY(cudaMemcpyToSymbol(c_inv_int, inv_int, sizeof(inv_int)));
+    CUDA_TRY(cudaMemcpyToSymbol(c_half_n, half_n, sizeof(half_n)));
     g_prog.vrr[dev] = v;
     g_prog.hrr[dev] = h;
     g_prog.acc[dev] = a;
@@ -151,9 +166,8 @@ ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
 }
 
 template <typename Real, int MODE>
-int launch_class(const DevBasis &B, const DevProgs &PR, const ClassLaunch &cl, const WorkItem *items,
-                 int nitems, int ket_base, const JKArgs &a, cudaStream_t st) {
-  if (nitems <= 0) return LTJK_OK;
+int launch_class(const DevProgs &PR, const ClassLaunch &cl, const JobTable &T, cudaStream_t st) {
+  if (T.total <= 0) return LTJK_OK;
   const size_t smem = (size_t)cl.smem_per_warp * cl.warps;
   if (smem > (size_t)kMaxSmem)
     return set_error(LTJK_EUNSUPPORTED, "class (%d%d|%d%d) needs %zu bytes of shared memory",
@@ -164,11 +178,25 @@ int launch_class(const DevBasis &B, const DevProgs &PR, const ClassLaunch &cl, c
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     attr_set = true;
   }
-  const int ctas_needed = (nitems + cl.warps - 1) / cl.warps;
+  const int ctas_needed = (T.total + cl.warps - 1) / cl.warps;
   const int grid = std::min(ctas_needed, 152 * 32);
-  quartet_kernel<Real, MODE><<<grid, 32 * cl.warps, smem, st>>>(B, PR, cl, items, nitems, ket_base, a);
+  quartet_kernel<Real, MODE><<<grid, 32 * cl.warps, smem, st>>>(PR, cl, T);
   CUDA_TRY(cudaGetLastError());
+  g_launches += 1;
   return LTJK_OK;
+}
+
+// A launch over one job.
+JobTable single_job(const DevBasis &B, const JKArgs &a, const WorkItem *items, int n) {
+  JobTable T;
+  T.njobs = 1;
+  T.total = n;
+  T.j[0].B = B;
+  T.j[0].a = a;
+  T.j[0].items = items;
+  T.j[0].nitems = n;
+  T.j[0].first = 0;
+  return T;
 }
 
 }  // namespace
@@ -299,7 +327,7 @@ int store_blocks(ltjk_ctx &c, const std::vector<std::pair<int, int>> &qs, int pr
     std::vector<WorkItem> items;
     std::vector<long long> ioff;
     for (int k : kv.second) {
-      items.push_back(WorkItem{qs[k].first, qs[k].second, 1, 0});
+      items.push_back(WorkItem{qs[k].first, qs[k].second, 1, 0});  // absolute ket pair
       ioff.push_back(offsets[k]);
     }
     DevBuf d_items, d_off;
@@ -309,12 +337,12 @@ int store_blocks(ltjk_ctx &c, const std::vector<std::pair<int, int>> &qs, int pr
     a.out_off = d_off.as<long long>();
     if (prec == LTJK_FP64) {
       ClassLaunch cl = make_launch(p, sizeof(double));
-      rc = launch_class<double, kStore>(B, c.progs, cl, d_items.as<WorkItem>(), (int)items.size(), 0,
-                                        a, st);
+      rc = launch_class<double, kStore>(c.progs, cl,
+                                        single_job(B, a, d_items.as<WorkItem>(), (int)items.size()), st);
     } else {
       ClassLaunch cl = make_launch(p, sizeof(float));
-      rc = launch_class<float, kStore>(B, c.progs, cl, d_items.as<WorkItem>(), (int)items.size(), 0,
-                                       a, st);
+      rc = launch_class<float, kStore>(c.progs, cl,
+                                       single_job(B, a, d_items.as<WorkItem>(), (int)items.size()), st);
     }
     if (rc) return rc;
     CUDA_TRY(cudaStreamSynchronize(st));  // the temporary item lists die here
@@ -388,9 +416,9 @@ int build_work(ltjk_ctx &c) {
           }
           n64 = lo;
         }
-        for (int k = 0; k < n64; k += kKetChunk) i64.push_back({i, k, std::min(kKetChunk, n64 - k), 0});
+        for (int k = 0; k < n64; k += kKetChunk) i64.push_back({i, yb + k, std::min(kKetChunk, n64 - k), 0});
         for (int k = n64; k < nkeep; k += kKetChunk)
-          i32.push_back({i, k, std::min(kKetChunk, nkeep - k), 0});
+          i32.push_back({i, yb + k, std::min(kKetChunk, nkeep - k), 0});
         c.stats.quartets_kept += nkeep;
         c.stats.quartets_fp64 += n64;
         long long npq = 0;
@@ -413,6 +441,12 @@ int build_work(ltjk_ctx &c) {
 extern "C" {
 
 const char *ltjk_last_error(void) { return last_error(); }
+
+int ltjk_launch_count(unsigned long long *count) {
+  if (!count) return set_error(LTJK_EINVAL, "launch_count: null argument");
+  *count = g_launches.load();
+  return LTJK_OK;
+}
 int ltjk_version(void) { return 100; }
 
 int ltjk_context_create(const ltjk_basis *bs, const ltjk_opts *opts, ltjk_ctx **out) {
@@ -595,16 +629,22 @@ int ltjk_jk_build(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *
   CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t NN = (size_t)ctx->nao * ctx->nao, n = NN * ndens;
-  int rc = ctx->ensure_scratch(4 * n * sizeof(double));
+  const bool mixed = ctx->opts.precision == LTJK_MIXED;
+  int rc = ctx->ensure_scratch(4 * n * sizeof(double) + (mixed ? 2 * n * sizeof(float) : 0));
   if (rc) return rc;
   double *Dq = ctx->scratch.as<double>(), *Sq = Dq + n, *Jq = Sq + n, *Kq = Jq + n;
+  float *Dq32 = mixed ? reinterpret_cast<float *>(Kq + n) : nullptr;
+  float *Sq32 = mixed ? Dq32 + n : nullptr;
   const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-  to_qinner<<<blocks, 256, 0, st>>>(D, Dq, Sq, ndens, ctx->nao);
+  to_qinner<<<blocks, 256, 0, st>>>(D, Dq, Sq, Dq32, Sq32, ndens, ctx->nao);
   CUDA_TRY(cudaGetLastError());
+  g_launches += 1;
   CUDA_TRY(cudaMemsetAsync(Jq, 0, 2 * n * sizeof(double), st));
   JKArgs a{};
   a.D = Dq;
   a.S = Sq;
+  a.D32 = Dq32;
+  a.S32 = Sq32;
   a.J = J ? Jq : nullptr;
   a.K = K ? Kq : nullptr;
   a.nd = ndens;
@@ -615,19 +655,18 @@ int ltjk_jk_build(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *
     const ClassProg &p = ps->progs[quartet_index(w->la, w->lb, w->lc, w->ld, 0)];
     if (w->n64) {
       ClassLaunch cl = make_launch(p, sizeof(double));
-      if ((rc = launch_class<double, kJK>(B, ctx->progs, cl, w->items64.as<WorkItem>(), w->n64,
-                                          w->ket_base, a, st)))
+      if ((rc = launch_class<double, kJK>(ctx->progs, cl, single_job(B, a, w->items64.as<WorkItem>(), w->n64), st)))
         return rc;
     }
     if (w->n32) {
       ClassLaunch cl = make_launch(p, sizeof(float));
-      if ((rc = launch_class<float, kJK>(B, ctx->progs, cl, w->items32.as<WorkItem>(), w->n32,
-                                         w->ket_base, a, st)))
+      if ((rc = launch_class<float, kJK>(ctx->progs, cl, single_job(B, a, w->items32.as<WorkItem>(), w->n32), st)))
         return rc;
     }
   }
   from_qinner<<<blocks, 256, 0, st>>>(Jq, Kq, J, K, ndens, ctx->nao);
   CUDA_TRY(cudaGetLastError());
+  g_launches += 1;
   return LTJK_OK;
 }
 
@@ -642,9 +681,10 @@ int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, do
   if (rc) return rc;
   double *Pq = ctx->scratch.as<double>(), *Qq = Pq + n;
   const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-  to_qinner<<<blocks, 256, 0, st>>>(P, Pq, nullptr, nterms, ctx->nao);
-  to_qinner<<<blocks, 256, 0, st>>>(Q, Qq, nullptr, nterms, ctx->nao);
+  to_qinner<<<blocks, 256, 0, st>>>(P, Pq, nullptr, nullptr, nullptr, nterms, ctx->nao);
+  to_qinner<<<blocks, 256, 0, st>>>(Q, Qq, nullptr, nullptr, nullptr, nterms, ctx->nao);
   CUDA_TRY(cudaGetLastError());
+  g_launches += 2;
   CUDA_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 3 * ctx->natoms, st));
   JKArgs a{};
   a.P = Pq;
@@ -660,14 +700,12 @@ int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, do
     const ClassProg &p = ps->progs[quartet_index(w->la, w->lb, w->lc, w->ld, 1)];
     if (w->n64) {
       ClassLaunch cl = make_launch(p, sizeof(double));
-      if ((rc = launch_class<double, kGrad>(B, ctx->progs, cl, w->items64.as<WorkItem>(), w->n64,
-                                            w->ket_base, a, st)))
+      if ((rc = launch_class<double, kGrad>(ctx->progs, cl, single_job(B, a, w->items64.as<WorkItem>(), w->n64), st)))
         return rc;
     }
     if (w->n32) {
       ClassLaunch cl = make_launch(p, sizeof(float));
-      if ((rc = launch_class<float, kGrad>(B, ctx->progs, cl, w->items32.as<WorkItem>(), w->n32,
-                                           w->ket_base, a, st)))
+      if ((rc = launch_class<float, kGrad>(ctx->progs, cl, single_job(B, a, w->items32.as<WorkItem>(), w->n32), st)))
         return rc;
     }
   }
@@ -702,6 +740,7 @@ int ltjk_pseudo_densities(ltjk_ctx *ctx, int nocc, int nvir, const double *C_occ
   gemm_f64<false><<<g2, thr, 0, st>>>(C_occ, 0, Z, (long long)nocc * N, D, (long long)N * N, N, N,
                                       nocc, nocc, N, N);
   CUDA_TRY(cudaGetLastError());
+  g_launches += 3;
   return LTJK_OK;
 }
 
@@ -729,3 +768,5 @@ int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int preci
 }
 
 }  // extern "C"
+
+#include "service.cuh"

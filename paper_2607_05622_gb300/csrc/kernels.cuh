@@ -9,37 +9,47 @@
 namespace ltjk {
 
 // ------------------------------------------------------------------ Boys
-// F_m(T) = int_0^1 u^{2m} exp(-T u^2) du.  For T < kBoysTmax: 8-term Taylor
-// expansion of F_mmax about the nearest tabulated point (dF_m/dT = -F_{m+1}),
-// then the downward relation F_m = (2T F_{m+1} + e^{-T}) / (2m+1).  Otherwise
-// F_0 = (1/2) sqrt(pi/T) (erf(sqrt T) = 1 to double precision there) and the
-// upward relation F_{m+1} = ((2m+1) F_m - e^{-T}) / (2T).  The table is filled on
-// the host by Gauss-Legendre quadrature of the defining integral.
+// F_m(T) = int_0^1 u^{2m} exp(-T u^2) du.  For T < kBoysTmax: Taylor expansion
+// about the nearest tabulated point T_k (dF_m/dT = -F_{m+1}), with the table
+// holding F_{m+j}(T_k)/j! so that each order costs kBoysTaylor-1 FMAs.  Low
+// orders (mmax <= 4) are all expanded directly; higher ones expand F_mmax and
+// descend with F_m = (2T F_{m+1} + e^{-T}) / (2m+1).  For T >= kBoysTmax:
+// F_0 = (1/2) sqrt(pi/T) (erf(sqrt T) = 1 in double precision there) and
+// F_{m+1} = ((2m+1) F_m - e^{-T}) / (2T).  The table is filled on the host by
+// Gauss-Legendre quadrature of the defining integral.
 constexpr double kBoysStep = 0.05;
 constexpr double kBoysInvStep = 20.0;
 constexpr double kBoysTmax = 40.0;
 constexpr int kBoysRows = 801;                 // T_k = k * step, k = 0..800
-constexpr int kBoysTaylor = 8;
-constexpr int kBoysCols = kBoysMaxM + kBoysTaylor;  // m = 0 .. kBoysMaxM + 7
+constexpr int kBoysTaylor = 8;                 // terms; |T - T_k| <= 0.025
+constexpr int kBoysM = kBoysMaxM + 1;          // orders tabulated
+constexpr int kBoysRaw = kBoysMaxM + kBoysTaylor;  // orders needed to fill the table
 
-__constant__ double c_inv_odd[kBoysCols + 2];   // 1/(2m+1)
-__constant__ double c_inv_int[kBoysTaylor + 1]; // 1/j
+__constant__ double c_inv_odd[kBoysRaw + 2];   // 1/(2m+1)
+__constant__ double c_half_n[2 * kMaxLDeriv + 4];  // n/2
+
+__device__ __forceinline__ double boys_taylor(const double *__restrict__ row, double x) {
+  double f = __ldg(row + kBoysTaylor - 1);
+#pragma unroll
+  for (int j = kBoysTaylor - 2; j >= 0; --j) f = fma(f, x, __ldg(row + j));
+  return f;
+}
 
 __device__ __forceinline__ void boys_eval(int mmax, double T, const double *__restrict__ tab,
                                           double *F) {
   if (T < kBoysTmax) {
-    int k = __double2int_rn(T * kBoysInvStep);
-    double x = k * kBoysStep - T;  // -(T - T_k)
-    const double *row = tab + k * kBoysCols + mmax;
-    double f = __ldg(row + kBoysTaylor - 1);
-#pragma unroll
-    for (int j = kBoysTaylor - 2; j >= 0; --j) f = fma(f, x * c_inv_int[j + 1], __ldg(row + j));
-    F[mmax] = f;
-    double e = exp(-T);
-    for (int m = mmax - 1; m >= 0; --m) F[m] = fma(2.0 * T, F[m + 1], e) * c_inv_odd[m];
+    const int k = __double2int_rn(T * kBoysInvStep);
+    const double x = k * kBoysStep - T;  // -(T - T_k)
+    const double *row = tab + (size_t)k * kBoysM * kBoysTaylor;
+    if (mmax <= 4) {
+      for (int m = 0; m <= mmax; ++m) F[m] = boys_taylor(row + m * kBoysTaylor, x);
+    } else {
+      F[mmax] = boys_taylor(row + mmax * kBoysTaylor, x);
+      const double e = exp(-T), T2 = 2.0 * T;
+      for (int m = mmax - 1; m >= 0; --m) F[m] = fma(T2, F[m + 1], e) * c_inv_odd[m];
+    }
   } else {
-    double e = exp(-T);
-    double inv2T = 0.5 / T;
+    const double e = exp(-T), inv2T = 0.5 / T;
     F[0] = 0.88622692545275801365 * rsqrt(T);  // (1/2) sqrt(pi/T)
     for (int m = 0; m < mmax; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) * inv2T;
   }
@@ -68,7 +78,7 @@ struct DevProgs {
   const TileProg *tiles;
 };
 
-// Work item: bra pair, ket pairs [k0, k0 + nk).
+// Work item: bra pair, ket pairs [k0, k0 + nk) (absolute pair indices).
 struct WorkItem {
   int bra, k0, nk, pad;
 };
@@ -79,6 +89,8 @@ struct JKArgs {
   // q-innermost layouts: X[(mu*N + nu)*nd + q]
   const double *D;   // densities
   const double *S;   // D + D^T
+  const float *D32;  // FP32 copies for the FP32 quartets (mixed precision)
+  const float *S32;
   double *J;         // half-Coulomb accumulator (symmetrised afterwards)
   double *K;
   int nd;
@@ -89,6 +101,23 @@ struct JKArgs {
   const double *P, *Q;  // q-innermost term stacks, nd = nterms
   double cJ, cK;
   double *grad;         // [natoms][3]
+};
+
+// One job of a launch: a context's basis and buffers and its slice of the
+// class's work list.  A launch carries up to kMaxJobs jobs by value in its
+// parameter block, so work items of several requests share one kernel.
+constexpr int kMaxJobs = 24;
+struct JobDesc {
+  DevBasis B;
+  JKArgs a;
+  const WorkItem *items;
+  int nitems;
+  int first;  // index of this job's first item in the launch
+};
+struct JobTable {
+  int njobs;
+  int total;
+  JobDesc j[kMaxJobs];
 };
 
 // Per-primitive-quartet table entry layout (Real units):
@@ -183,10 +212,10 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
       cf[kWB] = Real(2.0 * B.pp_b[ia]);
       cf[kWC] = Real(2.0 * B.pp_a[ic]);
       Real *h = cf + kNumCoef;
-      for (int n = 0; n < kNmax; ++n) {
-        h[n] = Real(0.5 * n * izeta);
-        h[kNmax + n] = Real(0.5 * n * ieta);
-        h[2 * kNmax + n] = Real(0.5 * n * isum);
+      for (int n = 0; n < p.nh; ++n) {
+        h[n] = Real(c_half_n[n] * izeta);
+        h[kNmax + n] = Real(c_half_n[n] * ieta);
+        h[2 * kNmax + n] = Real(c_half_n[n] * isum);
       }
     }
     __syncwarp();
@@ -210,9 +239,11 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
             const int kd = in.kind, d = in.dir;
             Real t = cf[kPAx + 3 * kd + d] * my_vrr[in.s0];
             t = fma(cf[kWPx + 3 * kd + d], my_vrr[in.s1], t);
-            Real u = fma(-cf[kRhoZeta + kd], my_vrr[in.s3], my_vrr[in.s2]);
-            t = fma(h[kd * kNmax + in.n1], u, t);
-            t = fma(h[2 * kNmax + in.n2], my_vrr[in.s4], t);
+            if (in.n1) {
+              const Real u = fma(-cf[kRhoZeta + kd], my_vrr[in.s3], my_vrr[in.s2]);
+              t = fma(h[kd * kNmax + in.n1], u, t);
+            }
+            if (in.n2) t = fma(h[2 * kNmax + in.n2], my_vrr[in.s4], t);
             my_vrr[in.tgt] = t;
           }
         }
@@ -280,14 +311,18 @@ __constant__ Placement c_place[10] = {
     {2, 0, 3, 1, 0}, {3, 0, 2, 1, 0}, {2, 1, 3, 0, 0}, {3, 1, 2, 0, 0}};
 
 template <typename Real>
-__device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], const int n[4],
-                          double w, int N, int lane) {
+__device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], const int n[4], int N,
+                          int lane) {
   const int str[4] = {n[1] * n[2] * n[3], n[2] * n[3], n[3], 1};
   const int nd = a.nd;
   for (int pl = 0; pl < 10; ++pl) {
     const Placement P = c_place[pl];
     if (P.isJ ? a.J == nullptr : a.K == nullptr) continue;
-    const double *M = P.isJ ? a.S : a.D;
+    const Real *M;
+    if constexpr (sizeof(Real) == sizeof(double))
+      M = reinterpret_cast<const Real *>(P.isJ ? a.S : a.D);
+    else
+      M = reinterpret_cast<const Real *>(P.isJ ? a.S32 : a.D32);
     double *T = P.isJ ? a.J : a.K;
     const int nr = n[P.orow], nc = n[P.ocol], nu = n[P.srow], nv = n[P.scol];
     const int sr = str[P.orow], sc = str[P.ocol], su = str[P.srow], sv = str[P.scol];
@@ -296,12 +331,12 @@ __device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], cons
       const int q = t % nd, o = t / nd;
       const int x = o / nc, y = o % nc;
       const Real *Ib = I + x * sr + y * sc;
-      const double *Mb = M + ((size_t)off[P.srow] * N + off[P.scol]) * nd + q;
+      const Real *Mb = M + ((size_t)off[P.srow] * N + off[P.scol]) * nd + q;
       Real acc = Real(0);
       for (int u = 0; u < nu; ++u)
         for (int v = 0; v < nv; ++v)
-          acc = fma(Ib[u * su + v * sv], Real(__ldg(Mb + ((size_t)u * N + v) * nd)), acc);
-      atomicAdd(T + ((size_t)(off[P.orow] + x) * N + off[P.ocol] + y) * nd + q, w * (double)acc);
+          acc = fma(Ib[u * su + v * sv], __ldg(Mb + ((size_t)u * N + v) * nd), acc);
+      atomicAdd(T + ((size_t)(off[P.orow] + x) * N + off[P.ocol] + y) * nd + q, (double)acc);
     }
   }
 }
@@ -339,21 +374,26 @@ __device__ void gamma_block(const JKArgs &a, double *gam, const int off[4], cons
 // ------------------------------------------------------------- the kernel
 // One warp per work item (bra pair, ket range); warps of a CTA are independent.
 template <typename Real, int MODE>
-__global__ void __launch_bounds__(128) quartet_kernel(DevBasis B, DevProgs PR, ClassLaunch CL,
-                                                      const WorkItem *__restrict__ items, int nitems,
-                                                      int ket_base, JKArgs a) {
+__global__ void __launch_bounds__(128) quartet_kernel(DevProgs PR, ClassLaunch CL,
+                                                      const __grid_constant__ JobTable T) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const ClassProg &p = CL.p;
   unsigned char *wbase = smem_raw + (size_t)warp * CL.smem_per_warp;
   Real *sm = reinterpret_cast<Real *>(wbase);
   double *gam = reinterpret_cast<double *>(wbase + gamma_offset(p, CL.G, sizeof(Real)));
-  const int N = B.nao;
-  for (int it = blockIdx.x * CL.warps + warp; it < nitems; it += gridDim.x * CL.warps) {
-    const WorkItem W = items[it];
+  for (int it = blockIdx.x * CL.warps + warp; it < T.total; it += gridDim.x * CL.warps) {
+    int jb = 0;  // job holding item it (jobs are few; linear search in the parameter block)
+    while (jb + 1 < T.njobs && it >= T.j[jb + 1].first) ++jb;
+    const JobDesc &J = T.j[jb];
+    const DevBasis &B = J.B;
+    const JKArgs &a = J.a;
+    const int N = B.nao;
+    const int li = it - J.first;
+    const WorkItem W = J.items[li];
     const int2 sab = B.pair_sh[W.bra];
     for (int kk = 0; kk < W.nk; ++kk) {
-      const int jp = ket_base + W.k0 + kk;
+      const int jp = W.k0 + kk;
       const int2 scd = B.pair_sh[jp];
       Real *acc0 = quartet_block<Real>(B, PR, p, CL.G, sm, W.bra, jp, lane);
       const int sh[4] = {sab.x, sab.y, scd.x, scd.y};
@@ -371,10 +411,13 @@ __global__ void __launch_bounds__(128) quartet_kernel(DevBasis B, DevProgs PR, C
       for (int tile = 0; tile < p.ntile; ++tile) {
         const Real *I = hrr_tile<Real>(B, PR, p, tile, acc0, W.bra, jp, lane);
         if (MODE == kStore) {
-          double *o = a.out + a.out_off[it] + ((long long)kk * p.ntile + tile) * p.nout;
+          double *o = a.out + a.out_off[li] + ((long long)kk * p.ntile + tile) * p.nout;
           for (int t = lane; t < p.nout; t += 32) o[t] = (double)I[t];
         } else if (MODE == kJK) {
-          digest_jk<Real>(a, I, off, n, w, N, lane);
+          Real *Iw = const_cast<Real *>(I);
+          for (int t = lane; t < p.nout; t += 32) Iw[t] *= Real(w);  // degeneracy weight, once
+          __syncwarp();
+          digest_jk<Real>(a, I, off, n, N, lane);
         } else {
           double v = 0.0;
           for (int e = lane; e < p.nout; e += 32) v = fma((double)I[e], gam[e], v);
@@ -403,7 +446,8 @@ __global__ void __launch_bounds__(128) quartet_kernel(DevBasis B, DevProgs PR, C
 // --------------------------------------------------------- layout kernels
 // [nd][N][N] -> q-innermost [(mu*N+nu)*nd + q]; optionally also S = D + D^T.
 __global__ void to_qinner(const double *__restrict__ D, double *__restrict__ Dq,
-                          double *__restrict__ Sq, int nd, int N) {
+                          double *__restrict__ Sq, float *__restrict__ Dq32,
+                          float *__restrict__ Sq32, int nd, int N) {
   const size_t NN = (size_t)N * N;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < NN * nd;
        t += (size_t)gridDim.x * blockDim.x) {
@@ -412,7 +456,12 @@ __global__ void to_qinner(const double *__restrict__ D, double *__restrict__ Dq,
     const int mu = (int)(mn / N), nu = (int)(mn % N);
     const double v = D[q * NN + mn];
     Dq[t] = v;
-    if (Sq) Sq[t] = v + D[q * NN + (size_t)nu * N + mu];
+    if (Sq) {
+      const double sv = v + D[q * NN + (size_t)nu * N + mu];
+      Sq[t] = sv;
+      if (Sq32) Sq32[t] = (float)sv;
+    }
+    if (Dq32) Dq32[t] = (float)v;
   }
 }
 

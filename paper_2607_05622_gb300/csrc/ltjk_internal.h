@@ -88,6 +88,7 @@ struct ClassProg {
   int hrr_size;   // HRR slots beyond the accumulators, max over tiles (slot acc_total = zero)
   int acc_total;  // nchan * acc_size
   int nout;       // outputs per tile (na nb nc nd)
+  int nh;         // 1 + largest integer multiplier of a VRR step
   double vrr_flops, hrr_flops;  // flop model: per primitive quartet / per contracted quartet
 };
 

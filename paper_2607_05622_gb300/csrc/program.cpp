@@ -233,8 +233,15 @@ void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv
   {
     std::vector<int> order(vg.instr.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return vg.instr_level[x] < vg.instr_level[y]; });
+    // within a level, group steps by which optional terms they carry so that
+    // the lanes of a warp mostly take the same branch
+    auto type = [&](int k) { return (vg.instr[k].n1 ? 1 : 0) + (vg.instr[k].n2 ? 2 : 0); };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      if (vg.instr_level[x] != vg.instr_level[y]) return vg.instr_level[x] < vg.instr_level[y];
+      return type(x) < type(y);
+    });
+    P.nh = 1;
+    for (const VrrInstr &in : vg.instr) P.nh = std::max({P.nh, in.n1 + 1, in.n2 + 1});
     P.vrr_begin = (int)ps.vrr.size();
     P.vrr_level0 = (int)ps.levels.size();
     int cur = -1;

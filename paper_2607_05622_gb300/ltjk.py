@@ -57,6 +57,7 @@ _P, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 SIGNATURES = {
     "ltjk_last_error": ([], ctypes.c_char_p),
     "ltjk_version": ([], _I),
+    "ltjk_launch_count": ([_P], _I),
     "ltjk_context_create": ([_P, _P, _P], _I),
     "ltjk_context_destroy": ([_P], _I),
     "ltjk_nao": ([_P, _P], _I),
@@ -67,6 +68,14 @@ SIGNATURES = {
     "ltjk_jk_build": ([_P, _I, _P, _P, _P, _P], _I),
     "ltjk_jk_grad": ([_P, _I, _P, _P, _D, _D, _P, _P], _I),
     "ltjk_shell_quartets": ([_P, _I, _P, _I, _P, _P], _I),
+    "ltjk_service_create": ([ctypes.c_size_t, _I, _P], _I),
+    "ltjk_service_submit": ([_P, _P, _P], _I),
+    "ltjk_service_poll": ([_P, ctypes.c_uint64, _P], _I),
+    "ltjk_service_wait": ([_P, ctypes.c_uint64, _D], _I),
+    "ltjk_service_cancel": ([_P, ctypes.c_uint64], _I),
+    "ltjk_service_stats": ([_P, _P], _I),
+    "ltjk_service_fail_next_admission": ([_P, _I], _I),
+    "ltjk_service_destroy": ([_P], _I),
 }
 
 
@@ -105,6 +114,13 @@ def _dev(t: torch.Tensor, shape=None, name="tensor"):
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    c = ctypes.c_ulonglong(0)
+    _check(lib().ltjk_launch_count(ctypes.byref(c)))
+    return c.value
 
 
 def laplace_quadrature(xmin: float, xmax: float, n: int):
@@ -257,3 +273,104 @@ class JKEnergy(torch.autograd.Function):
             J, K = c.jk_build(P.detach().contiguous())
             gQ = (ctx_.cJ * J + ctx_.cK * K) * gE
         return gc, gP, gQ, None, None, None, None
+
+
+REQ_JK, REQ_GRAD = 0, 1
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("ctx", ctypes.c_void_p), ("n", ctypes.c_int),
+                ("D", ctypes.c_void_p), ("J", ctypes.c_void_p), ("K", ctypes.c_void_p),
+                ("P", ctypes.c_void_p), ("Q", ctypes.c_void_p), ("cJ", ctypes.c_double),
+                ("cK", ctypes.c_double), ("grad", ctypes.c_void_p)]
+
+
+class ServiceStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("throughput_rps", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t),
+                ("bytes_peak", ctypes.c_size_t), ("budget", ctypes.c_size_t),
+                ("steps", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("active", ctypes.c_int), ("queued", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Service:
+    """Continuous-batching J/K and gradient service (ltjk_service_* in include/ltjk.h).
+
+    Tensors passed to submit_* must stay alive and unmodified until the request
+    finishes; the binding keeps references until wait() returns."""
+
+    def __init__(self, hbm_budget_bytes: int, device: int = 0):
+        h = ctypes.c_void_p()
+        torch.cuda.set_device(device)
+        _check(lib().ltjk_service_create(int(hbm_budget_bytes), int(device), ctypes.byref(h)))
+        self._h = h
+        self.device = device
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().ltjk_service_destroy(self._h))
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _submit(self, req, keep):
+        torch.cuda.current_stream().synchronize()  # inputs complete on the device
+        t = ctypes.c_uint64()
+        _check(lib().ltjk_service_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = keep
+        return t.value
+
+    def submit_jk(self, ctx: Context, D, J=None, K=None):
+        nd, N = D.shape[0], ctx.nao
+        if J is None:
+            J = torch.empty_like(D)
+        if K is None:
+            K = torch.empty_like(D)
+        req = _Request(REQ_JK, ctx._h.value, nd, _dev(D, (nd, N, N), "D").value,
+                       _dev(J, (nd, N, N), "J").value, _dev(K, (nd, N, N), "K").value,
+                       None, None, 0.0, 0.0, None)
+        return self._submit(req, (ctx, D, J, K)), J, K
+
+    def submit_grad(self, ctx: Context, P, Q, cJ=1.0, cK=0.0, grad=None):
+        nt, N = P.shape[0], ctx.nao
+        if grad is None:
+            grad = torch.empty((ctx.natoms, 3), dtype=torch.float64, device=P.device)
+        req = _Request(REQ_GRAD, ctx._h.value, nt, None, None, None,
+                       _dev(P, (nt, N, N), "P").value, _dev(Q, (nt, N, N), "Q").value,
+                       float(cJ), float(cK), _dev(grad, (ctx.natoms, 3), "grad").value)
+        return self._submit(req, (ctx, P, Q, grad)), grad
+
+    def poll(self, ticket):
+        done = ctypes.c_int(0)
+        rc = lib().ltjk_service_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(done))
+        if done.value:
+            self._keep.pop(ticket, None)
+        return bool(done.value), rc
+
+    def wait(self, ticket, timeout_s=60.0):
+        rc = lib().ltjk_service_wait(self._h, ctypes.c_uint64(ticket), float(timeout_s))
+        if rc != ETIMEDOUT:
+            self._keep.pop(ticket, None)
+        _check(rc)
+
+    def cancel(self, ticket):
+        _check(lib().ltjk_service_cancel(self._h, ctypes.c_uint64(ticket)))
+
+    def fail_next_admission(self, count=1):
+        _check(lib().ltjk_service_fail_next_admission(self._h, int(count)))
+
+    def stats(self) -> dict:
+        s = ServiceStats()
+        _check(lib().ltjk_service_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
