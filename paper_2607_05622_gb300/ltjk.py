@@ -257,6 +257,7 @@ class JKEnergy(torch.autograd.Function):
         ctx_.save_for_backward(P, Q, F)
         ctx_.c = c
         ctx_.cJ, ctx_.cK = cJ, cK
+        ctx_.coords_device = coords.device
         return E
 
     @staticmethod
@@ -265,8 +266,8 @@ class JKEnergy(torch.autograd.Function):
         c = ctx_.c
         gc = gP = gQ = None
         if ctx_.needs_input_grad[0]:
-            gc = c.jk_grad(P.detach().contiguous(), Q.detach().contiguous(), ctx_.cJ, ctx_.cK) * gE
-            gc = gc.to(P.device)
+            g = c.jk_grad(P.detach().contiguous(), Q.detach().contiguous(), ctx_.cJ, ctx_.cK)
+            gc = (g * gE).to(ctx_.coords_device)
         if ctx_.needs_input_grad[1]:
             gP = F * gE
         if ctx_.needs_input_grad[2]:
