@@ -169,6 +169,27 @@ int ltjk_pseudo_densities(ltjk_ctx *ctx, int nocc, int nvir, const double *C_occ
 int ltjk_jk_build(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *K,
                   ltjk_stream stream);
 
+/* The same build as ltjk_jk_build, but the call allocates no device memory:
+   its scratch is a fixed 64 MiB array inside the library (held by every GPU
+   that loads the library until the process exits).  This is for callers that
+   cannot let a library allocate: applications that own all device memory
+   through their own pool or framework allocator, or latency-critical loops
+   that cannot absorb the device-wide synchronisation of cudaMalloc/cudaFree.
+   The paper has no counterpart; this is an interface convenience.
+     Limit: 4 * ndens * N * N doubles (FP64 contexts) or 5 * ndens * N * N
+     (mixed contexts) must not exceed 8 * 2^20; larger requests return
+     LTJK_EINVAL with the sizes in ltjk_last_error().
+     The first call on each device looks up the array's device address
+     (cudaGetSymbolAddress) with that device current; make that first call
+     before any stream capture.
+     All calls share the one array and it keeps the previous call's contents
+     (the accumulators are cleared on every call): calls that can overlap on
+     the GPU (different streams, or different host threads) race and give
+     wrong results; serialise them.
+   Arguments, layouts and results are those of ltjk_jk_build. */
+int ltjk_jk_build_noalloc(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *K,
+                          ltjk_stream stream);
+
 /* ---------------------------------------------------------- gradient adjoint */
 /* grad[A][x] = d/dR_{A,x} sum_r [cJ J(P_r, Q_r) + cK K(P_r, Q_r)] with the
    ordered builds J(A,B) = sum (mu nu|ka rho) A_{mu nu} B_{ka rho} and

@@ -769,4 +769,89 @@ int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int preci
 
 }  // extern "C"
 
+// ------------------------------------------------- allocation-free J/K build
+// Scratch of ltjk_jk_build_noalloc: a file-scope device array, so the call
+// itself never allocates.  Every device that loads this library holds it
+// (64 MiB) until the process exits.  Host code must not pass the symbol
+// itself to a kernel (on the host it names a stand-in, not device memory);
+// the device address is looked up once per device with cudaGetSymbolAddress.
+namespace {
+constexpr size_t kNoallocDoubles = size_t(8) << 20;  // 64 MiB of FP64 scratch
+__device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+std::mutex g_noalloc_mu;
+std::map<int, double *> g_noalloc_ptr;  // device -> address of g_noalloc_scratch
+
+int noalloc_scratch(int device, double **out) {
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  auto it = g_noalloc_ptr.find(device);
+  if (it != g_noalloc_ptr.end()) {
+    *out = it->second;
+    return LTJK_OK;
+  }
+  double *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return set_error(LTJK_ECUDA, "jk_build_noalloc: cudaGetSymbolAddress failed: %s",
+                     cudaGetErrorString(e));
+  g_noalloc_ptr[device] = p;
+  *out = p;
+  return LTJK_OK;
+}
+}  // namespace
+
+extern "C" int ltjk_jk_build_noalloc(ltjk_ctx *ctx, int ndens, const double *D, double *J,
+                                     double *K, ltjk_stream stream) {
+  if (!ctx || !D) return set_error(LTJK_EINVAL, "jk_build_noalloc: null context or density");
+  if (ndens < 1 || ndens > 4096)
+    return set_error(LTJK_EINVAL, "jk_build_noalloc: ndens %d not in 1..4096", ndens);
+  if (!J && !K) return LTJK_OK;
+  const bool mixed = ctx->opts.precision == LTJK_MIXED;
+  const size_t NN = (size_t)ctx->nao * ctx->nao, n = NN * ndens;
+  const size_t need = 4 * n + (mixed ? n : 0);  // Dq, Sq, Jq, Kq (+ two FP32 copies)
+  if (need > kNoallocDoubles)
+    return set_error(LTJK_EINVAL,
+                     "jk_build_noalloc: %d densities of %d AOs need %zu bytes of scratch, above the "
+                     "fixed %zu-byte limit (use ltjk_jk_build)",
+                     ndens, ctx->nao, need * sizeof(double), kNoallocDoubles * sizeof(double));
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  double *base = nullptr;
+  int rc = noalloc_scratch(ctx->device, &base);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  double *Dq = base, *Sq = Dq + n, *Jq = Sq + n, *Kq = Jq + n;
+  float *Dq32 = mixed ? reinterpret_cast<float *>(Kq + n) : nullptr;
+  float *Sq32 = mixed ? Dq32 + n : nullptr;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  to_qinner<<<blocks, 256, 0, st>>>(D, Dq, Sq, Dq32, Sq32, ndens, ctx->nao);
+  CUDA_TRY(cudaGetLastError());
+  g_launches += 1;
+  CUDA_TRY(cudaMemsetAsync(Jq, 0, 2 * n * sizeof(double), st));  // the array keeps old contents
+  JKArgs a{};
+  a.D = Dq;
+  a.S = Sq;
+  a.D32 = Dq32;
+  a.S32 = Sq32;
+  a.J = J ? Jq : nullptr;
+  a.K = K ? Kq : nullptr;
+  a.nd = ndens;
+  DevBasis B = ctx->basis();
+  const ProgramSet *ps;
+  if ((rc = program_set(&ps))) return rc;
+  for (auto &w : ctx->work) {
+    const ClassProg &p = ps->progs[quartet_index(w->la, w->lb, w->lc, w->ld, 0)];
+    if (w->n64 &&
+        (rc = launch_class<double, kJK>(ctx->progs, make_launch(p, sizeof(double)),
+                                        single_job(B, a, w->items64.as<WorkItem>(), w->n64), st)))
+      return rc;
+    if (w->n32 &&
+        (rc = launch_class<float, kJK>(ctx->progs, make_launch(p, sizeof(float)),
+                                       single_job(B, a, w->items32.as<WorkItem>(), w->n32), st)))
+      return rc;
+  }
+  from_qinner<<<blocks, 256, 0, st>>>(Jq, Kq, J, K, ndens, ctx->nao);
+  CUDA_TRY(cudaGetLastError());
+  g_launches += 1;
+  return LTJK_OK;
+}
+
 #include "service.cuh"

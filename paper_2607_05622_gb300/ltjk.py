@@ -66,6 +66,7 @@ SIGNATURES = {
     "ltjk_laplace_quadrature": ([_D, _D, _I, _P, _P, _P], _I),
     "ltjk_pseudo_densities": ([_P, _I, _I, _P, _P, _P, _P, _I, _P, _I, _P, _P, _P], _I),
     "ltjk_jk_build": ([_P, _I, _P, _P, _P, _P], _I),
+    "ltjk_jk_build_noalloc": ([_P, _I, _P, _P, _P, _P], _I),
     "ltjk_jk_grad": ([_P, _I, _P, _P, _D, _D, _P, _P], _I),
     "ltjk_shell_quartets": ([_P, _I, _P, _I, _P, _P], _I),
     "ltjk_service_create": ([ctypes.c_size_t, _I, _P], _I),
@@ -191,6 +192,15 @@ class Context:
         jp = _dev(J, (nd, N, N), "J") if want_j else None
         kp = _dev(K, (nd, N, N), "K") if want_k else None
         _check(lib().ltjk_jk_build(self._h, nd, dp, jp, kp, _stream(stream)))
+        return J, K
+
+    def jk_build_noalloc(self, D: torch.Tensor, J: torch.Tensor, K: torch.Tensor, stream=None):
+        """ltjk_jk_build_noalloc: the same build with the library's fixed scratch array;
+        the library allocates nothing (J and K are the caller's)."""
+        nd, N = D.shape[0], self.nao
+        _check(lib().ltjk_jk_build_noalloc(self._h, nd, _dev(D, (nd, N, N), "D"),
+                                           _dev(J, (nd, N, N), "J"), _dev(K, (nd, N, N), "K"),
+                                           _stream(stream)))
         return J, K
 
     def jk_grad(self, P: torch.Tensor, Q: torch.Tensor, cJ=1.0, cK=0.0, grad=None, stream=None):
