@@ -53,8 +53,9 @@ extern "C" {
 
 #define LTJK_MAX_L 2            /* largest shell angular momentum of the value build */
 
-#define LTJK_FP64 0
-#define LTJK_MIXED 1
+#define LTJK_FP64 0         /* FP64-class: double-float recurrences and digestion */
+#define LTJK_MIXED 1        /* FP32 below the Schwarz threshold, FP64-class above */
+#define LTJK_FP64_NATIVE 2  /* every recurrence and digestion step in IEEE binary64 */
 
 typedef struct CUstream_st *ltjk_stream;
 
@@ -95,9 +96,16 @@ typedef struct {
                   Q_ab = max over mu in a, nu in b of sqrt|(mu nu|mu nu)|
                   (plain Schwarz bound, not density weighted).  0 keeps all.
      mixed_tau    precision == LTJK_MIXED only: quartets with Q_ab*Q_cd > mixed_tau
-                  are evaluated in FP64, the rest in FP32 (Boys function always
+                  are evaluated FP64-class, the rest in FP32 (Boys function always
                   FP64; J/K always accumulated in FP64).
-     precision    LTJK_FP64 or LTJK_MIXED.
+     precision    LTJK_FP64, LTJK_MIXED or LTJK_FP64_NATIVE.  The Boys function,
+                  the per-primitive setup and the accumulation across quartets
+                  are IEEE FP64 in every mode.  LTJK_FP64 runs the recurrences
+                  and the density digestion in double-float arithmetic (pairs of
+                  FP32 words, about 2^-44 relative per operation) on the FP32
+                  pipe, which on GB300 is 58x faster than its FP64 pipe;
+                  LTJK_FP64_NATIVE keeps them in IEEE FP64.  Both meet the FP64
+                  parity gate (1e-10 relative to the oracle).
      device       CUDA device ordinal the context lives on. */
 typedef struct {
   double schwarz_tau;
@@ -205,7 +213,8 @@ int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, do
 /* Contracted Cartesian integral blocks of nq shell quartets (a,b|c,d) given in
    shells_host[4*nq]; out [sum of block sizes] device FP64, blocks concatenated
    in order, each [na][nb][nc][nd] row-major.  Evaluated by the same kernels as
-   the build, in FP64 (precision = LTJK_FP64) or FP32 (LTJK_MIXED). */
+   the build: double-float (LTJK_FP64), FP32 (LTJK_MIXED) or IEEE FP64
+   (LTJK_FP64_NATIVE). */
 int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int precision,
                         double *out, ltjk_stream stream);
 

@@ -29,7 +29,9 @@ namespace {
 
 std::atomic<unsigned long long> g_launches{0};  // kernels launched by this library
 
-constexpr int kKetChunk = 16;            // ket pairs per work item
+constexpr int kKetChunk = 16;            // most ket pairs per work item
+constexpr long long kTargetItems = 152 * 24;  // work items a class should offer the GPU
+constexpr int kSideStreams = 4;          // class launches of one build run on these concurrently
 constexpr int kSmemBudget = 200 * 1024;  // bytes of shared memory per CTA we plan for
 constexpr int kMaxSmem = 227 * 1024;
 constexpr double kPrimPairDrop = 1e-18;  // drop primitive pair iff K_AB |c_a c_b| below this
@@ -216,7 +218,7 @@ struct ltjk_ctx {
   std::map<std::pair<int, int>, int> pair_of;  // canonical (a,b) -> sorted pair index
   // device data
   DevBuf d_ctr, d_l, d_ao, d_atom, d_pair_sh, d_pair_pp0, d_pair_npp, d_pp_zeta, d_pp_izeta, d_pp_P,
-      d_pp_pref, d_pp_a, d_pp_b;
+      d_pp_pref, d_pp_a, d_pp_b, d_pp2, d_ctr2;
   DevProgs progs{};
   const double *boys = nullptr;
   std::vector<std::unique_ptr<ClassWork>> work;       // value build
@@ -224,6 +226,15 @@ struct ltjk_ctx {
   DevBuf scratch;
   DevBuf d_t;
   ltjk_ctx_stats stats{};
+  cudaStream_t side[kSideStreams] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
+  ~ltjk_ctx() {
+    for (int k = 0; k < kSideStreams; ++k) {
+      if (side[k]) cudaStreamDestroy(side[k]);
+      if (join_ev[k]) cudaEventDestroy(join_ev[k]);
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
+  }
 
   DevBasis basis() const {
     DevBasis B{};
@@ -240,6 +251,8 @@ struct ltjk_ctx {
     B.pp_pref = d_pp_pref.as<double>();
     B.pp_a = d_pp_a.as<double>();
     B.pp_b = d_pp_b.as<double>();
+    B.pp2 = d_pp2.as<float2>();
+    B.ctr2 = d_ctr2.as<float2>();
     B.boys = boys;
     B.nao = nao;
     return B;
@@ -259,7 +272,13 @@ struct HostPairs {
   std::vector<int2> sh;
   std::vector<int> cls, pp0, npp;
   std::vector<double> zeta, izeta, P, pref, a, b;
+  std::vector<float2> pp2;  // double-float copies, 8 per primitive pair
 };
+
+float2 split2(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
 
 void build_pairs(const ltjk_ctx &c, const std::vector<int2> &order, HostPairs &hp) {
   const double pi = 3.14159265358979323846;
@@ -286,6 +305,10 @@ void build_pairs(const ltjk_ctx &c, const std::vector<int2> &order, HostPairs &h
         hp.pref.push_back(s2pi52 * kab * ca * cb / z);
         hp.a.push_back(al);
         hp.b.push_back(be);
+        const double Pv[3] = {(al * A[0] + be * B[0]) / z, (al * A[1] + be * B[1]) / z,
+                              (al * A[2] + be * B[2]) / z};
+        for (double v : {z, 1.0 / z, Pv[0], Pv[1], Pv[2], s2pi52 * kab * ca * cb / z, al, be})
+          hp.pp2.push_back(split2(v));
         ++kept;
       }
     hp.npp.push_back(kept);
@@ -299,7 +322,7 @@ int upload_pairs(ltjk_ctx &c, const HostPairs &hp) {
       (rc = c.d_pair_npp.upload(hp.npp)) || (rc = c.d_pp_zeta.upload(hp.zeta)) ||
       (rc = c.d_pp_izeta.upload(hp.izeta)) || (rc = c.d_pp_P.upload(hp.P)) ||
       (rc = c.d_pp_pref.upload(hp.pref)) || (rc = c.d_pp_a.upload(hp.a)) ||
-      (rc = c.d_pp_b.upload(hp.b)))
+      (rc = c.d_pp_b.upload(hp.b)) || (rc = c.d_pp2.upload(hp.pp2)))
     return rc;
   return LTJK_OK;
 }
@@ -335,10 +358,14 @@ int store_blocks(ltjk_ctx &c, const std::vector<std::pair<int, int>> &qs, int pr
     JKArgs a{};
     a.out = d_out;
     a.out_off = d_off.as<long long>();
-    if (prec == LTJK_FP64) {
+    if (prec == LTJK_FP64_NATIVE) {
       ClassLaunch cl = make_launch(p, sizeof(double));
       rc = launch_class<double, kStore>(c.progs, cl,
                                         single_job(B, a, d_items.as<WorkItem>(), (int)items.size()), st);
+    } else if (prec == LTJK_FP64) {
+      ClassLaunch cl = make_launch(p, sizeof(dflt));
+      rc = launch_class<dflt, kStore>(c.progs, cl,
+                                      single_job(B, a, d_items.as<WorkItem>(), (int)items.size()), st);
     } else {
       ClassLaunch cl = make_launch(p, sizeof(float));
       rc = launch_class<float, kStore>(c.progs, cl,
@@ -393,7 +420,9 @@ int build_work(ltjk_ctx &c) {
       cw->ld = c.sh_l[t0.y];
       cw->ket_base = yb;
       const ClassProg &p = ps->progs[quartet_index(cw->la, cw->lb, cw->lc, cw->ld, 0)];
-      std::vector<WorkItem> i64, i32;
+      // Schwarz-kept ket prefix of every bra pair, split FP64-class / FP32
+      std::vector<int> keep(xe - xb), n64v(xe - xb);
+      long long tot64 = 0, tot32 = 0;
       for (int i = xb; i < xe; ++i) {
         const double qi = c.pair_Q[i];
         int nj = ye - yb;
@@ -416,9 +445,10 @@ int build_work(ltjk_ctx &c) {
           }
           n64 = lo;
         }
-        for (int k = 0; k < n64; k += kKetChunk) i64.push_back({i, yb + k, std::min(kKetChunk, n64 - k), 0});
-        for (int k = n64; k < nkeep; k += kKetChunk)
-          i32.push_back({i, yb + k, std::min(kKetChunk, nkeep - k), 0});
+        keep[i - xb] = nkeep;
+        n64v[i - xb] = n64;
+        tot64 += n64;
+        tot32 += nkeep - n64;
         c.stats.quartets_kept += nkeep;
         c.stats.quartets_fp64 += n64;
         long long npq = 0;
@@ -426,13 +456,105 @@ int build_work(ltjk_ctx &c) {
         c.stats.prim_quartets_kept += npq;
         c.stats.cart_integrals_kept +=
             (long long)nkeep * ncart(cw->la) * ncart(cw->lb) * ncart(cw->lc) * ncart(cw->ld);
-        c.stats.eri_flops_per_build += class_flops(p, npq) + (double)nkeep * 0.0;
+        c.stats.eri_flops_per_build += class_flops(p, npq);
+      }
+      // kets per work item: small enough that a class yields at least
+      // kTargetItems items (heavy classes have few quartets), at most kKetChunk
+      auto chunk_of = [](long long total) {
+        return (int)std::max<long long>(1, std::min<long long>(kKetChunk, (total + kTargetItems - 1) / kTargetItems));
+      };
+      const int ch64 = chunk_of(tot64), ch32 = chunk_of(tot32);
+      std::vector<WorkItem> i64, i32;
+      for (int i = xb; i < xe; ++i) {
+        const int nkeep = keep[i - xb], n64 = n64v[i - xb];
+        for (int k = 0; k < n64; k += ch64) i64.push_back({i, yb + k, std::min(ch64, n64 - k), 0});
+        for (int k = n64; k < nkeep; k += ch32) i32.push_back({i, yb + k, std::min(ch32, nkeep - k), 0});
       }
       if ((rc = cw->items64.upload(i64)) || (rc = cw->items32.upload(i32))) return rc;
       cw->n64 = (int)i64.size();
       cw->n32 = (int)i32.size();
       c.work.push_back(std::move(cw));
     }
+  return LTJK_OK;
+}
+
+
+// Device scratch of one J/K build of nd densities: two density copies, the J
+// and K accumulators (q-innermost), plus FP32 copies in mixed precision.
+size_t jk_scratch_bytes(const ltjk_ctx *c, int nd) {
+  const size_t n = (size_t)c->nao * c->nao * nd;
+  return 4 * n * sizeof(double) + (c->opts.precision == LTJK_MIXED ? 2 * n * sizeof(float) : 0);
+}
+
+// Enqueue the layout transposes and the accumulator clear of one J/K build
+// whose scratch starts at `base`; returns the kernel arguments.
+JKArgs jk_prologue(const ltjk_ctx *c, const double *D, void *base, int nd, bool wantJ, bool wantK,
+                   cudaStream_t st) {
+  const size_t n = (size_t)c->nao * c->nao * nd;
+  double *A = static_cast<double *>(base), *Bq = A + n, *Jq = Bq + n, *Kq = Jq + n;
+  const bool native = c->opts.precision == LTJK_FP64_NATIVE;
+  const bool mixed = c->opts.precision == LTJK_MIXED;
+  float *D32 = mixed ? reinterpret_cast<float *>(Kq + n) : nullptr;
+  float *S32 = mixed ? D32 + n : nullptr;
+  JKArgs a{};
+  if (native) {
+    a.D = A;
+    a.S = Bq;
+  } else {
+    a.D2 = reinterpret_cast<dflt *>(A);
+    a.S2 = reinterpret_cast<dflt *>(Bq);
+  }
+  a.D32 = D32;
+  a.S32 = S32;
+  a.J = wantJ ? Jq : nullptr;
+  a.K = wantK ? Kq : nullptr;
+  a.nd = nd;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  to_qinner<<<blocks, 256, 0, st>>>(D, native ? A : nullptr, native ? Bq : nullptr, D32, S32, nd,
+                                    c->nao, native ? nullptr : reinterpret_cast<dflt *>(A),
+                                    native ? nullptr : reinterpret_cast<dflt *>(Bq));
+  g_launches += 1;
+  cudaMemsetAsync(Jq, 0, 2 * n * sizeof(double), st);
+  return a;
+}
+
+// The class launches of one pass (J/K or gradient) over a context's work
+// lists: FP64-class items in double-float (native FP64 on request), FP32 items
+// (mixed precision) in float.
+template <int MODE>
+int launch_classes(ltjk_ctx *ctx, const JKArgs &a, cudaStream_t st) {
+  const ProgramSet *ps;
+  int rc = program_set(&ps);
+  if (rc) return rc;
+  const bool native = ctx->opts.precision == LTJK_FP64_NATIVE;
+  const DevBasis B = ctx->basis();
+  // fork: the class launches are independent (they only add into J, K or the
+  // gradient), so they run on the context's side streams concurrently, which
+  // keeps the GPU full while a heavy class with few work items runs
+  CUDA_TRY(cudaEventRecord(ctx->fork_ev, st));
+  for (int k = 0; k < kSideStreams; ++k) CUDA_TRY(cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0));
+  int next = 0;
+  for (auto &w : ctx->work) {
+    const ClassProg &p = ps->progs[quartet_index(w->la, w->lb, w->lc, w->ld, MODE == kGrad)];
+    if (w->n64) {
+      cudaStream_t s2 = ctx->side[next++ % kSideStreams];
+      const JobTable T = single_job(B, a, w->items64.as<WorkItem>(), w->n64);
+      rc = native ? launch_class<double, MODE>(ctx->progs, make_launch(p, sizeof(double)), T, s2)
+                  : launch_class<dflt, MODE>(ctx->progs, make_launch(p, sizeof(dflt)), T, s2);
+      if (rc) return rc;
+    }
+    if (w->n32) {
+      cudaStream_t s2 = ctx->side[next++ % kSideStreams];
+      if ((rc = launch_class<float, MODE>(ctx->progs, make_launch(p, sizeof(float)),
+                                          single_job(B, a, w->items32.as<WorkItem>(), w->n32), s2)))
+        return rc;
+    }
+  }
+  // join
+  for (int k = 0; k < kSideStreams; ++k) {
+    CUDA_TRY(cudaEventRecord(ctx->join_ev[k], ctx->side[k]));
+    CUDA_TRY(cudaStreamWaitEvent(st, ctx->join_ev[k], 0));
+  }
   return LTJK_OK;
 }
 
@@ -455,8 +577,10 @@ int ltjk_context_create(const ltjk_basis *bs, const ltjk_opts *opts, ltjk_ctx **
   if (bs->natoms <= 0 || bs->nshells <= 0 || !bs->coords_host || !bs->shell_atom_host ||
       !bs->shell_l_host || !bs->shell_nprim_host || !bs->exps_host || !bs->coefs_host)
     return set_error(LTJK_EINVAL, "context_create: empty or incomplete basis");
-  if (opts->precision != LTJK_FP64 && opts->precision != LTJK_MIXED)
-    return set_error(LTJK_EINVAL, "context_create: precision must be LTJK_FP64 or LTJK_MIXED");
+  if (opts->precision != LTJK_FP64 && opts->precision != LTJK_MIXED &&
+      opts->precision != LTJK_FP64_NATIVE)
+    return set_error(LTJK_EINVAL,
+                     "context_create: precision must be LTJK_FP64, LTJK_MIXED or LTJK_FP64_NATIVE");
   if (!(opts->schwarz_tau >= 0) || !(opts->mixed_tau >= 0))
     return set_error(LTJK_EINVAL, "context_create: thresholds must be >= 0");
   auto c = std::make_unique<ltjk_ctx>();
@@ -493,10 +617,18 @@ int ltjk_context_create(const ltjk_basis *bs, const ltjk_opts *opts, ltjk_ctx **
                     &c->ncoef[c->sh_p0[s]]);
   int rc;
   if ((rc = device_programs(c->device, &c->progs, &c->boys))) return rc;
+  CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+  for (int k = 0; k < kSideStreams; ++k) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&c->join_ev[k], cudaEventDisableTiming));
+  }
   std::vector<double> ctr(3 * c->nshells);
   for (int s = 0; s < c->nshells; ++s)
     for (int x = 0; x < 3; ++x) ctr[3 * s + x] = c->coords[3 * c->sh_atom[s] + x];
-  if ((rc = c->d_ctr.upload(ctr)) || (rc = c->d_l.upload(c->sh_l)) || (rc = c->d_ao.upload(c->sh_ao)) ||
+  std::vector<float2> ctr2;
+  for (double v : ctr) ctr2.push_back(split2(v));
+  if ((rc = c->d_ctr.upload(ctr)) || (rc = c->d_ctr2.upload(ctr2)) || (rc = c->d_l.upload(c->sh_l)) ||
+      (rc = c->d_ao.upload(c->sh_ao)) ||
       (rc = c->d_atom.upload(c->sh_atom)))
     return rc;
   // canonical pairs grouped by class: l_a >= l_b, and a >= b when l_a == l_b
@@ -529,7 +661,7 @@ int ltjk_context_create(const ltjk_basis *bs, const ltjk_opts *opts, ltjk_ctx **
     DevBuf d_out;
     if ((rc = d_out.alloc(sizeof(double) * std::max<long long>(total, 1)))) return rc;
     std::vector<long long> offs;
-    if ((rc = store_blocks(*c, qs, LTJK_FP64, offs, d_out.as<double>(), 0))) return rc;
+    if ((rc = store_blocks(*c, qs, LTJK_FP64_NATIVE, offs, d_out.as<double>(), 0))) return rc;
     std::vector<double> blocks(total);
     CUDA_TRY(cudaMemcpy(blocks.data(), d_out.p, sizeof(double) * total, cudaMemcpyDeviceToHost));
     c->pair_Q.assign(c->npairs, 0.0);
@@ -628,43 +760,14 @@ int ltjk_jk_build(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *
   if (!J && !K) return LTJK_OK;
   CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const size_t NN = (size_t)ctx->nao * ctx->nao, n = NN * ndens;
-  const bool mixed = ctx->opts.precision == LTJK_MIXED;
-  int rc = ctx->ensure_scratch(4 * n * sizeof(double) + (mixed ? 2 * n * sizeof(float) : 0));
+  const size_t n = (size_t)ctx->nao * ctx->nao * ndens;
+  int rc = ctx->ensure_scratch(jk_scratch_bytes(ctx, ndens));
   if (rc) return rc;
-  double *Dq = ctx->scratch.as<double>(), *Sq = Dq + n, *Jq = Sq + n, *Kq = Jq + n;
-  float *Dq32 = mixed ? reinterpret_cast<float *>(Kq + n) : nullptr;
-  float *Sq32 = mixed ? Dq32 + n : nullptr;
-  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-  to_qinner<<<blocks, 256, 0, st>>>(D, Dq, Sq, Dq32, Sq32, ndens, ctx->nao);
+  const JKArgs a = jk_prologue(ctx, D, ctx->scratch.p, ndens, J != nullptr, K != nullptr, st);
   CUDA_TRY(cudaGetLastError());
-  g_launches += 1;
-  CUDA_TRY(cudaMemsetAsync(Jq, 0, 2 * n * sizeof(double), st));
-  JKArgs a{};
-  a.D = Dq;
-  a.S = Sq;
-  a.D32 = Dq32;
-  a.S32 = Sq32;
-  a.J = J ? Jq : nullptr;
-  a.K = K ? Kq : nullptr;
-  a.nd = ndens;
-  DevBasis B = ctx->basis();
-  const ProgramSet *ps;
-  if ((rc = program_set(&ps))) return rc;
-  for (auto &w : ctx->work) {
-    const ClassProg &p = ps->progs[quartet_index(w->la, w->lb, w->lc, w->ld, 0)];
-    if (w->n64) {
-      ClassLaunch cl = make_launch(p, sizeof(double));
-      if ((rc = launch_class<double, kJK>(ctx->progs, cl, single_job(B, a, w->items64.as<WorkItem>(), w->n64), st)))
-        return rc;
-    }
-    if (w->n32) {
-      ClassLaunch cl = make_launch(p, sizeof(float));
-      if ((rc = launch_class<float, kJK>(ctx->progs, cl, single_job(B, a, w->items32.as<WorkItem>(), w->n32), st)))
-        return rc;
-    }
-  }
-  from_qinner<<<blocks, 256, 0, st>>>(Jq, Kq, J, K, ndens, ctx->nao);
+  if ((rc = launch_classes<kJK>(ctx, a, st))) return rc;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  from_qinner<<<blocks, 256, 0, st>>>(a.J, a.K, J, K, ndens, ctx->nao);
   CUDA_TRY(cudaGetLastError());
   g_launches += 1;
   return LTJK_OK;
@@ -693,23 +796,7 @@ int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, do
   a.cJ = cJ;
   a.cK = cK;
   a.grad = grad;
-  DevBasis B = ctx->basis();
-  const ProgramSet *ps;
-  if ((rc = program_set(&ps))) return rc;
-  for (auto &w : ctx->work) {
-    const ClassProg &p = ps->progs[quartet_index(w->la, w->lb, w->lc, w->ld, 1)];
-    if (w->n64) {
-      ClassLaunch cl = make_launch(p, sizeof(double));
-      if ((rc = launch_class<double, kGrad>(ctx->progs, cl, single_job(B, a, w->items64.as<WorkItem>(), w->n64), st)))
-        return rc;
-    }
-    if (w->n32) {
-      ClassLaunch cl = make_launch(p, sizeof(float));
-      if ((rc = launch_class<float, kGrad>(ctx->progs, cl, single_job(B, a, w->items32.as<WorkItem>(), w->n32), st)))
-        return rc;
-    }
-  }
-  return LTJK_OK;
+  return launch_classes<kGrad>(ctx, a, st);
 }
 
 int ltjk_pseudo_densities(ltjk_ctx *ctx, int nocc, int nvir, const double *C_occ,
@@ -747,7 +834,7 @@ int ltjk_pseudo_densities(ltjk_ctx *ctx, int nocc, int nvir, const double *C_occ
 int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int precision, double *out,
                         ltjk_stream stream) {
   if (!ctx || !shells_host || !out || nq < 0) return set_error(LTJK_EINVAL, "shell_quartets: bad argument");
-  if (precision != LTJK_FP64 && precision != LTJK_MIXED)
+  if (precision != LTJK_FP64 && precision != LTJK_MIXED && precision != LTJK_FP64_NATIVE)
     return set_error(LTJK_EINVAL, "shell_quartets: bad precision");
   CUDA_TRY(cudaSetDevice(ctx->device));
   std::vector<std::pair<int, int>> qs;
@@ -805,9 +892,8 @@ extern "C" int ltjk_jk_build_noalloc(ltjk_ctx *ctx, int ndens, const double *D, 
   if (ndens < 1 || ndens > 4096)
     return set_error(LTJK_EINVAL, "jk_build_noalloc: ndens %d not in 1..4096", ndens);
   if (!J && !K) return LTJK_OK;
-  const bool mixed = ctx->opts.precision == LTJK_MIXED;
-  const size_t NN = (size_t)ctx->nao * ctx->nao, n = NN * ndens;
-  const size_t need = 4 * n + (mixed ? n : 0);  // Dq, Sq, Jq, Kq (+ two FP32 copies)
+  const size_t n = (size_t)ctx->nao * ctx->nao * ndens;
+  const size_t need = jk_scratch_bytes(ctx, ndens) / sizeof(double);  // 4 (or 5) n doubles
   if (need > kNoallocDoubles)
     return set_error(LTJK_EINVAL,
                      "jk_build_noalloc: %d densities of %d AOs need %zu bytes of scratch, above the "
@@ -818,37 +904,12 @@ extern "C" int ltjk_jk_build_noalloc(ltjk_ctx *ctx, int ndens, const double *D, 
   int rc = noalloc_scratch(ctx->device, &base);
   if (rc) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  double *Dq = base, *Sq = Dq + n, *Jq = Sq + n, *Kq = Jq + n;
-  float *Dq32 = mixed ? reinterpret_cast<float *>(Kq + n) : nullptr;
-  float *Sq32 = mixed ? Dq32 + n : nullptr;
-  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-  to_qinner<<<blocks, 256, 0, st>>>(D, Dq, Sq, Dq32, Sq32, ndens, ctx->nao);
+  // the array keeps the previous call's contents; the prologue clears the accumulators
+  const JKArgs a = jk_prologue(ctx, D, base, ndens, J != nullptr, K != nullptr, st);
   CUDA_TRY(cudaGetLastError());
-  g_launches += 1;
-  CUDA_TRY(cudaMemsetAsync(Jq, 0, 2 * n * sizeof(double), st));  // the array keeps old contents
-  JKArgs a{};
-  a.D = Dq;
-  a.S = Sq;
-  a.D32 = Dq32;
-  a.S32 = Sq32;
-  a.J = J ? Jq : nullptr;
-  a.K = K ? Kq : nullptr;
-  a.nd = ndens;
-  DevBasis B = ctx->basis();
-  const ProgramSet *ps;
-  if ((rc = program_set(&ps))) return rc;
-  for (auto &w : ctx->work) {
-    const ClassProg &p = ps->progs[quartet_index(w->la, w->lb, w->lc, w->ld, 0)];
-    if (w->n64 &&
-        (rc = launch_class<double, kJK>(ctx->progs, make_launch(p, sizeof(double)),
-                                        single_job(B, a, w->items64.as<WorkItem>(), w->n64), st)))
-      return rc;
-    if (w->n32 &&
-        (rc = launch_class<float, kJK>(ctx->progs, make_launch(p, sizeof(float)),
-                                       single_job(B, a, w->items32.as<WorkItem>(), w->n32), st)))
-      return rc;
-  }
-  from_qinner<<<blocks, 256, 0, st>>>(Jq, Kq, J, K, ndens, ctx->nao);
+  if ((rc = launch_classes<kJK>(ctx, a, st))) return rc;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  from_qinner<<<blocks, 256, 0, st>>>(a.J, a.K, J, K, ndens, ctx->nao);
   CUDA_TRY(cudaGetLastError());
   g_launches += 1;
   return LTJK_OK;

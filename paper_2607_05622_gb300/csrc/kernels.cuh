@@ -4,6 +4,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
 #include "ltjk_internal.h"
 
 namespace ltjk {
@@ -66,6 +67,8 @@ struct DevBasis {
   const int *pair_npp;   // number of primitive pairs kept
   // primitive pairs
   const double *pp_zeta, *pp_inv_zeta, *pp_P, *pp_pref, *pp_a, *pp_b;  // pp_P: [npp][3]
+  const float2 *pp2;     // the same as double-float pairs: [npp][8] = zeta, 1/zeta, P, pref, alpha, beta
+  const float2 *ctr2;    // shell centres as double-float pairs [nshells][3]
   const double *boys;    // [kBoysRows][kBoysCols]
   int nao;
 };
@@ -91,6 +94,8 @@ struct JKArgs {
   const double *S;   // D + D^T
   const float *D32;  // FP32 copies for the FP32 quartets (mixed precision)
   const float *S32;
+  const dflt *D2;    // double-float copies for the double-float quartets
+  const dflt *S2;
   double *J;         // half-Coulomb accumulator (symmetrised afterwards)
   double *K;
   int nd;
@@ -123,9 +128,9 @@ struct JobTable {
 // Per-primitive-quartet table entry layout (Real units):
 //   [0 .. ltot]           base values [00|00]^(m)
 //   [ltot+1 .. +kNumCoef) coefficients (CoefSlot order)
-//   then hz[0..nmax], he[0..nmax], hs[0..nmax]: n/(2 zeta), n/(2 eta), n/(2(zeta+eta))
+//   then hz[0..nh), he[0..nh), hs[0..nh): n/(2 zeta), n/(2 eta), n/(2(zeta+eta))
 constexpr int kNmax = 2 * kMaxLDeriv + 2;  // largest integer multiplier + 1
-__host__ __device__ inline int pt_stride(int ltot) { return ltot + 1 + kNumCoef + 3 * kNmax; }
+__host__ __device__ inline int pt_stride(const ClassProg &p) { return p.ltot + 1 + kNumCoef + 3 * p.nh; }
 
 struct ClassLaunch {
   ClassProg p;
@@ -139,15 +144,128 @@ struct ClassLaunch {
 // the gradient the Gamma block of one quartet (double).
 __host__ __device__ inline size_t warp_smem_bytes(const ClassProg &p, int G, size_t real_bytes) {
   int work = G * p.vrr_size > p.hrr_size ? G * p.vrr_size : p.hrr_size;
-  size_t b = (size_t)(32 * pt_stride(p.ltot) + G * p.acc_total + work) * real_bytes;
+  size_t b = (size_t)(32 * pt_stride(p) + G * p.acc_total + work) * real_bytes;
   b = (b + 15) / 16 * 16;
   if (p.deriv) b += (size_t)p.nout * sizeof(double);
   return (b + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t gamma_offset(const ClassProg &p, int G, size_t real_bytes) {
   int work = G * p.vrr_size > p.hrr_size ? G * p.vrr_size : p.hrr_size;
-  size_t b = (size_t)(32 * pt_stride(p.ltot) + G * p.acc_total + work) * real_bytes;
+  size_t b = (size_t)(32 * pt_stride(p) + G * p.acc_total + work) * real_bytes;
   return (b + 15) / 16 * 16;
+}
+
+// ------------------------------------------- stage 1: one primitive quartet
+// Base values [00|00]^(m) = 2 pi^{5/2} K_AB K_CD c.. / (zeta eta sqrt(zeta+eta))
+// F_m(rho |PQ|^2) and the Obara-Saika coefficients of primitive pairs ia
+// (bra) and ic (ket), written to the table entry e.
+template <typename Real>
+__device__ __forceinline__ void stage1(const DevBasis &B, const ClassProg &p, Real *e, int ia, int ic,
+                                       int2 sab, int2 scd);
+
+// IEEE FP64 throughout.
+template <>
+__device__ __forceinline__ void stage1<double>(const DevBasis &B, const ClassProg &p, double *e, int ia,
+                                               int ic, int2 sab, int2 scd) {
+  const double *A = B.sh_ctr + 3 * sab.x, *C = B.sh_ctr + 3 * scd.x;
+  const double zeta = B.pp_zeta[ia], eta = B.pp_zeta[ic];
+  const double izeta = B.pp_inv_zeta[ia], ieta = B.pp_inv_zeta[ic];
+  const double *P = B.pp_P + 3 * ia, *Q = B.pp_P + 3 * ic;
+  const double isum = 1.0 / (zeta + eta);
+  const double rho = zeta * eta * isum;
+  double PQ2 = 0.0, W[3];
+  for (int x = 0; x < 3; ++x) {
+    double d = P[x] - Q[x];
+    PQ2 = fma(d, d, PQ2);
+    W[x] = (zeta * P[x] + eta * Q[x]) * isum;
+  }
+  double F[kBoysMaxM + 1];
+  boys_eval(p.ltot, rho * PQ2, B.boys, F);
+  const double pre = B.pp_pref[ia] * B.pp_pref[ic] * sqrt(isum);
+  for (int m = 0; m <= p.ltot; ++m) e[m] = pre * F[m];
+  double *cf = e + p.ltot + 1;
+  for (int x = 0; x < 3; ++x) {
+    cf[kPAx + x] = P[x] - A[x];
+    cf[kQCx + x] = Q[x] - C[x];
+    cf[kWPx + x] = W[x] - P[x];
+    cf[kWQx + x] = W[x] - Q[x];
+  }
+  cf[kHalfZeta] = 0.5 * izeta;
+  cf[kHalfEta] = 0.5 * ieta;
+  cf[kRhoZeta] = rho * izeta;
+  cf[kRhoEta] = rho * ieta;
+  cf[kHalfSum] = 0.5 * isum;
+  cf[kWA] = 2.0 * B.pp_a[ia];
+  cf[kWB] = 2.0 * B.pp_b[ia];
+  cf[kWC] = 2.0 * B.pp_a[ic];
+  double *h = cf + kNumCoef;
+  const int nh = p.nh;
+  for (int n = 0; n < nh; ++n) {
+    h[n] = c_half_n[n] * izeta;
+    h[nh + n] = c_half_n[n] * ieta;
+    h[2 * nh + n] = c_half_n[n] * isum;
+  }
+}
+
+__device__ __forceinline__ dflt df_load(const float2 *p) {
+  const float2 v = __ldg(p);
+  return dflt(v.x, v.y);
+}
+template <typename Real>
+__device__ __forceinline__ Real df_cvt(dflt x);
+template <>
+__device__ __forceinline__ dflt df_cvt<dflt>(dflt x) { return x; }
+template <>
+__device__ __forceinline__ float df_cvt<float>(dflt x) { return df_to_float(x); }
+
+// Double-float throughout on the FP32 pipe, except the Boys function (IEEE
+// FP64, its argument rounded once from double-float to double).
+template <typename Real>
+__device__ __forceinline__ void stage1(const DevBasis &B, const ClassProg &p, Real *e, int ia, int ic,
+                                       int2 sab, int2 scd) {
+  const float2 *pa = B.pp2 + 8 * ia, *pc = B.pp2 + 8 * ic;
+  const float2 *A = B.ctr2 + 3 * sab.x, *C = B.ctr2 + 3 * scd.x;
+  const dflt zeta = df_load(pa + 0), eta = df_load(pc + 0);
+  const dflt izeta = df_load(pa + 1), ieta = df_load(pc + 1);
+  const dflt isum = df_recip(zeta + eta);
+  const dflt rho = zeta * eta * isum;
+  dflt PQ2(0.0f, 0.0f), P[3], Q[3];
+  for (int x = 0; x < 3; ++x) {
+    P[x] = df_load(pa + 2 + x);
+    Q[x] = df_load(pc + 2 + x);
+    const dflt d = P[x] - Q[x];
+    PQ2 = fma(d, d, PQ2);
+  }
+  double F[kBoysMaxM + 1];
+  boys_eval(p.ltot, to_double(rho * PQ2), B.boys, F);
+  const dflt pre = df_load(pa + 5) * df_load(pc + 5) * df_sqrt(isum);
+  for (int m = 0; m <= p.ltot; ++m) e[m] = df_cvt<Real>(pre * dflt(F[m]));
+  Real *cf = e + p.ltot + 1;
+  for (int x = 0; x < 3; ++x) {
+    const dflt W = (zeta * P[x] + eta * Q[x]) * isum;
+    cf[kPAx + x] = df_cvt<Real>(P[x] - df_load(A + x));
+    cf[kQCx + x] = df_cvt<Real>(Q[x] - df_load(C + x));
+    cf[kWPx + x] = df_cvt<Real>(W - P[x]);
+    cf[kWQx + x] = df_cvt<Real>(W - Q[x]);
+  }
+  cf[kHalfZeta] = df_cvt<Real>(df_mulf(izeta, 0.5f));
+  cf[kHalfEta] = df_cvt<Real>(df_mulf(ieta, 0.5f));
+  cf[kRhoZeta] = df_cvt<Real>(rho * izeta);
+  cf[kRhoEta] = df_cvt<Real>(rho * ieta);
+  cf[kHalfSum] = df_cvt<Real>(df_mulf(isum, 0.5f));
+  if (p.deriv) {
+    cf[kWA] = df_cvt<Real>(df_mulf(df_load(pa + 6), 2.0f));
+    cf[kWB] = df_cvt<Real>(df_mulf(df_load(pa + 7), 2.0f));
+    cf[kWC] = df_cvt<Real>(df_mulf(df_load(pc + 6), 2.0f));
+  }
+  Real *h = cf + kNumCoef;
+  const int nh = p.nh;
+  for (int n = 0; n < nh; ++n) {
+    const float hn = 0.5f * (float)n;
+    h[n] = df_cvt<Real>(df_mulf(izeta, hn));
+    h[nh + n] = df_cvt<Real>(df_mulf(ieta, hn));
+    h[2 * nh + n] = df_cvt<Real>(df_mulf(isum, hn));
+  }
 }
 
 // ------------------------------------------------ one contracted quartet
@@ -158,7 +276,7 @@ template <typename Real>
 __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const ClassProg &p, int G,
                                Real *sm, int ip, int jp, int lane) {
   const int S = 32 / G, g = lane / S, s = lane % S;
-  const int stride = pt_stride(p.ltot);
+  const int stride = pt_stride(p), nh = p.nh;
   Real *ptab = sm;                              // [32][stride]
   Real *accs = ptab + 32 * stride;              // [G][acc_total]; group 0's last
   Real *acc0 = accs + (G - 1) * p.acc_total;
@@ -167,56 +285,18 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
   Real *my_vrr = work + g * p.vrr_size;
 
   const int2 sab = B.pair_sh[ip], scd = B.pair_sh[jp];
-  const double *A = B.sh_ctr + 3 * sab.x, *Bc = B.sh_ctr + 3 * sab.y;
-  const double *C = B.sh_ctr + 3 * scd.x, *Dc = B.sh_ctr + 3 * scd.y;
   const int pp0 = B.pair_pp0[ip], npp = B.pair_npp[ip];
   const int qq0 = B.pair_pp0[jp], nqq = B.pair_npp[jp];
   const int npq = npp * nqq;
 
-  for (int t = lane; t < G * p.acc_total; t += 32) accs[t] = Real(0);
+  for (int t = lane; t < G * p.acc_total; t += 32) accs[t] = zero_real<Real>();
 
   for (int c0 = 0; c0 < npq; c0 += 32) {
     // stage 1: base values and coefficients, one primitive quartet per lane
     const int pq = c0 + lane;
     if (pq < npq) {
       const int ia = pp0 + pq / nqq, ic = qq0 + pq % nqq;
-      const double zeta = B.pp_zeta[ia], eta = B.pp_zeta[ic];
-      const double izeta = B.pp_inv_zeta[ia], ieta = B.pp_inv_zeta[ic];
-      const double *P = B.pp_P + 3 * ia, *Q = B.pp_P + 3 * ic;
-      const double isum = 1.0 / (zeta + eta);
-      const double rho = zeta * eta * isum;
-      double PQ2 = 0.0, W[3];
-      for (int x = 0; x < 3; ++x) {
-        double d = P[x] - Q[x];
-        PQ2 = fma(d, d, PQ2);
-        W[x] = (zeta * P[x] + eta * Q[x]) * isum;
-      }
-      double F[kBoysMaxM + 1];
-      boys_eval(p.ltot, rho * PQ2, B.boys, F);
-      const double pre = B.pp_pref[ia] * B.pp_pref[ic] * sqrt(isum);
-      Real *e = ptab + lane * stride;
-      for (int m = 0; m <= p.ltot; ++m) e[m] = Real(pre * F[m]);
-      Real *cf = e + p.ltot + 1;
-      for (int x = 0; x < 3; ++x) {
-        cf[kPAx + x] = Real(P[x] - A[x]);
-        cf[kQCx + x] = Real(Q[x] - C[x]);
-        cf[kWPx + x] = Real(W[x] - P[x]);
-        cf[kWQx + x] = Real(W[x] - Q[x]);
-      }
-      cf[kHalfZeta] = Real(0.5 * izeta);
-      cf[kHalfEta] = Real(0.5 * ieta);
-      cf[kRhoZeta] = Real(rho * izeta);
-      cf[kRhoEta] = Real(rho * ieta);
-      cf[kHalfSum] = Real(0.5 * isum);
-      cf[kWA] = Real(2.0 * B.pp_a[ia]);
-      cf[kWB] = Real(2.0 * B.pp_b[ia]);
-      cf[kWC] = Real(2.0 * B.pp_a[ic]);
-      Real *h = cf + kNumCoef;
-      for (int n = 0; n < p.nh; ++n) {
-        h[n] = Real(c_half_n[n] * izeta);
-        h[kNmax + n] = Real(c_half_n[n] * ieta);
-        h[2 * kNmax + n] = Real(c_half_n[n] * isum);
-      }
+      stage1<Real>(B, p, ptab + lane * stride, ia, ic, sab, scd);
     }
     __syncwarp();
     // stage 2: recurrences, G primitive quartets at a time
@@ -228,7 +308,7 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
       const Real *cf = e + p.ltot + 1;
       const Real *h = cf + kNumCoef;
       if (active) {
-        for (int t = s; t <= p.ltot + 1; t += S) my_vrr[t] = t == 0 ? Real(0) : e[t - 1];
+        for (int t = s; t <= p.ltot + 1; t += S) my_vrr[t] = t == 0 ? zero_real<Real>() : e[t - 1];
       }
       __syncwarp();
       for (int L = 0; L < p.nvrr_level; ++L) {
@@ -241,9 +321,9 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
             t = fma(cf[kWPx + 3 * kd + d], my_vrr[in.s1], t);
             if (in.n1) {
               const Real u = fma(-cf[kRhoZeta + kd], my_vrr[in.s3], my_vrr[in.s2]);
-              t = fma(h[kd * kNmax + in.n1], u, t);
+              t = fma(h[kd * nh + in.n1], u, t);
             }
-            if (in.n2) t = fma(h[2 * kNmax + in.n2], my_vrr[in.s4], t);
+            if (in.n2) t = fma(h[2 * nh + in.n2], my_vrr[in.s4], t);
             my_vrr[in.tgt] = t;
           }
         }
@@ -280,12 +360,12 @@ __device__ Real *hrr_tile(const DevBasis &B, const DevProgs &PR, const ClassProg
   const int2 sab = B.pair_sh[ip], scd = B.pair_sh[jp];
   const double *A = B.sh_ctr + 3 * sab.x, *Bc = B.sh_ctr + 3 * sab.y;
   const double *C = B.sh_ctr + 3 * scd.x, *Dc = B.sh_ctr + 3 * scd.y;
-  if (lane == 0) acc0[p.acc_total] = Real(0);  // zero slot
+  if (lane == 0) acc0[p.acc_total] = zero_real<Real>();  // zero slot
   __syncwarp();
   Real X[2][3];
   for (int x = 0; x < 3; ++x) {
-    X[0][x] = Real(A[x] - Bc[x]);
-    X[1][x] = Real(C[x] - Dc[x]);
+    X[0][x] = from_double<Real>(A[x] - Bc[x]);
+    X[1][x] = from_double<Real>(C[x] - Dc[x]);
   }
   for (int L = 0; L < T.nhrr_level; ++L) {
     const int i0 = PR.levels[T.hrr_level0 + L], i1 = PR.levels[T.hrr_level0 + L + 1];
@@ -311,6 +391,21 @@ __constant__ Placement c_place[10] = {
     {2, 0, 3, 1, 0}, {3, 0, 2, 1, 0}, {2, 1, 3, 0, 0}, {3, 1, 2, 0, 0}};
 
 template <typename Real>
+__device__ __forceinline__ const Real *digest_operand(const JKArgs &a, bool isJ);
+template <>
+__device__ __forceinline__ const double *digest_operand<double>(const JKArgs &a, bool isJ) {
+  return isJ ? a.S : a.D;
+}
+template <>
+__device__ __forceinline__ const float *digest_operand<float>(const JKArgs &a, bool isJ) {
+  return isJ ? a.S32 : a.D32;
+}
+template <>
+__device__ __forceinline__ const dflt *digest_operand<dflt>(const JKArgs &a, bool isJ) {
+  return isJ ? a.S2 : a.D2;
+}
+
+template <typename Real>
 __device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], const int n[4], int N,
                           int lane) {
   const int str[4] = {n[1] * n[2] * n[3], n[2] * n[3], n[3], 1};
@@ -318,11 +413,7 @@ __device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], cons
   for (int pl = 0; pl < 10; ++pl) {
     const Placement P = c_place[pl];
     if (P.isJ ? a.J == nullptr : a.K == nullptr) continue;
-    const Real *M;
-    if constexpr (sizeof(Real) == sizeof(double))
-      M = reinterpret_cast<const Real *>(P.isJ ? a.S : a.D);
-    else
-      M = reinterpret_cast<const Real *>(P.isJ ? a.S32 : a.D32);
+    const Real *M = digest_operand<Real>(a, P.isJ);
     double *T = P.isJ ? a.J : a.K;
     const int nr = n[P.orow], nc = n[P.ocol], nu = n[P.srow], nv = n[P.scol];
     const int sr = str[P.orow], sc = str[P.ocol], su = str[P.srow], sv = str[P.scol];
@@ -332,11 +423,10 @@ __device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], cons
       const int x = o / nc, y = o % nc;
       const Real *Ib = I + x * sr + y * sc;
       const Real *Mb = M + ((size_t)off[P.srow] * N + off[P.scol]) * nd + q;
-      Real acc = Real(0);
+      Real acc = zero_real<Real>();
       for (int u = 0; u < nu; ++u)
-        for (int v = 0; v < nv; ++v)
-          acc = fma(Ib[u * su + v * sv], __ldg(Mb + ((size_t)u * N + v) * nd), acc);
-      atomicAdd(T + ((size_t)(off[P.orow] + x) * N + off[P.ocol] + y) * nd + q, (double)acc);
+        for (int v = 0; v < nv; ++v) acc = fma(Ib[u * su + v * sv], ldg(Mb + ((size_t)u * N + v) * nd), acc);
+      atomicAdd(T + ((size_t)(off[P.orow] + x) * N + off[P.ocol] + y) * nd + q, to_double(acc));
     }
   }
 }
@@ -403,24 +493,25 @@ __global__ void __launch_bounds__(128) quartet_kernel(DevProgs PR, ClassLaunch C
         n[t] = ncart(B.sh_l[sh[t]]);
       }
       double w = 1.0;
-      if (sab.x == sab.y) w *= 0.5;
-      if (scd.x == scd.y) w *= 0.5;
-      if (W.bra == jp) w *= 0.5;
+      float wf = 1.0f;
+      if (sab.x == sab.y) { w *= 0.5; wf *= 0.5f; }
+      if (scd.x == scd.y) { w *= 0.5; wf *= 0.5f; }
+      if (W.bra == jp) { w *= 0.5; wf *= 0.5f; }
       if (MODE == kGrad) gamma_block(a, gam, off, n, w, N, lane);
       double g9 = 0.0;  // lane t < 9 keeps component t
       for (int tile = 0; tile < p.ntile; ++tile) {
         const Real *I = hrr_tile<Real>(B, PR, p, tile, acc0, W.bra, jp, lane);
         if (MODE == kStore) {
           double *o = a.out + a.out_off[li] + ((long long)kk * p.ntile + tile) * p.nout;
-          for (int t = lane; t < p.nout; t += 32) o[t] = (double)I[t];
+          for (int t = lane; t < p.nout; t += 32) o[t] = to_double(I[t]);
         } else if (MODE == kJK) {
           Real *Iw = const_cast<Real *>(I);
-          for (int t = lane; t < p.nout; t += 32) Iw[t] *= Real(w);  // degeneracy weight, once
+          for (int t = lane; t < p.nout; t += 32) Iw[t] = scale_pow2(Iw[t], wf);  // degeneracy weight, once
           __syncwarp();
           digest_jk<Real>(a, I, off, n, N, lane);
         } else {
           double v = 0.0;
-          for (int e = lane; e < p.nout; e += 32) v = fma((double)I[e], gam[e], v);
+          for (int e = lane; e < p.nout; e += 32) v = fma(to_double(I[e]), gam[e], v);
           for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
           if (lane == tile) g9 = v;
         }
@@ -444,10 +535,12 @@ __global__ void __launch_bounds__(128) quartet_kernel(DevProgs PR, ClassLaunch C
 }
 
 // --------------------------------------------------------- layout kernels
-// [nd][N][N] -> q-innermost [(mu*N+nu)*nd + q]; optionally also S = D + D^T.
+// [nd][N][N] -> q-innermost [(mu*N+nu)*nd + q] copies of D and of S = D + D^T:
+// FP64 (Dq, Sq), double-float pairs (D2, S2) and FP32 (D32, S32); null = skip.
 __global__ void to_qinner(const double *__restrict__ D, double *__restrict__ Dq,
                           double *__restrict__ Sq, float *__restrict__ Dq32,
-                          float *__restrict__ Sq32, int nd, int N) {
+                          float *__restrict__ Sq32, int nd, int N, dflt *__restrict__ D2 = nullptr,
+                          dflt *__restrict__ S2 = nullptr) {
   const size_t NN = (size_t)N * N;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < NN * nd;
        t += (size_t)gridDim.x * blockDim.x) {
@@ -455,13 +548,13 @@ __global__ void to_qinner(const double *__restrict__ D, double *__restrict__ Dq,
     const size_t mn = t / nd;
     const int mu = (int)(mn / N), nu = (int)(mn % N);
     const double v = D[q * NN + mn];
-    Dq[t] = v;
-    if (Sq) {
-      const double sv = v + D[q * NN + (size_t)nu * N + mu];
-      Sq[t] = sv;
-      if (Sq32) Sq32[t] = (float)sv;
-    }
+    const double sv = v + D[q * NN + (size_t)nu * N + mu];
+    if (Dq) Dq[t] = v;
+    if (Sq) Sq[t] = sv;
     if (Dq32) Dq32[t] = (float)v;
+    if (Sq32) Sq32[t] = (float)sv;
+    if (D2) D2[t] = dflt(v);
+    if (S2) S2[t] = dflt(sv);
   }
 }
 

@@ -4,7 +4,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ltjk.h"
+#include "ltjk.h"
 
 namespace ltjk {
 

@@ -118,7 +118,7 @@ namespace {
 
 size_t job_bytes(const ltjk_request &r, int nao, bool mixed) {
   const size_t n = (size_t)nao * nao * r.n;
-  if (r.kind == LTJK_REQ_JK) return 4 * n * sizeof(double) + (mixed ? 2 * n * sizeof(float) : 0);
+  if (r.kind == LTJK_REQ_JK) return 4 * n * sizeof(double) + (mixed ? 2 * n * sizeof(float) : 0);  // = jk_scratch_bytes
   return 2 * n * sizeof(double);
 }
 
@@ -143,7 +143,7 @@ int ltjk_service::step(std::vector<SvcJob *> &run) {
   if (program_set(&ps)) return -1;
   int nl = 0;
   for (int mode = 0; mode < 2; ++mode)
-    for (int prec = 0; prec < 2; ++prec)
+    for (int prec = 0; prec < 3; ++prec)
       for (int q = 0; q < kNumPairClass * kNumPairClass; ++q) {
         JobTable T;
         T.njobs = 0;
@@ -151,16 +151,21 @@ int ltjk_service::step(std::vector<SvcJob *> &run) {
         const ClassProg *prog = nullptr;
         auto flush = [&]() {
           if (T.total == 0) return;
+          const DevProgs &PR = run[0]->req.ctx->progs;
           if (mode == 0) {
             if (prec == 0)
-              launch_class<double, kJK>(run[0]->req.ctx->progs, make_launch(*prog, sizeof(double)), T, st);
+              launch_class<dflt, kJK>(PR, make_launch(*prog, sizeof(dflt)), T, st);
+            else if (prec == 1)
+              launch_class<float, kJK>(PR, make_launch(*prog, sizeof(float)), T, st);
             else
-              launch_class<float, kJK>(run[0]->req.ctx->progs, make_launch(*prog, sizeof(float)), T, st);
+              launch_class<double, kJK>(PR, make_launch(*prog, sizeof(double)), T, st);
           } else {
             if (prec == 0)
-              launch_class<double, kGrad>(run[0]->req.ctx->progs, make_launch(*prog, sizeof(double)), T, st);
+              launch_class<dflt, kGrad>(PR, make_launch(*prog, sizeof(dflt)), T, st);
+            else if (prec == 1)
+              launch_class<float, kGrad>(PR, make_launch(*prog, sizeof(float)), T, st);
             else
-              launch_class<float, kGrad>(run[0]->req.ctx->progs, make_launch(*prog, sizeof(float)), T, st);
+              launch_class<double, kGrad>(PR, make_launch(*prog, sizeof(double)), T, st);
           }
           ++nl;
           T.njobs = 0;
@@ -169,18 +174,20 @@ int ltjk_service::step(std::vector<SvcJob *> &run) {
         for (SvcJob *j : run) {
           if ((j->req.kind == LTJK_REQ_JK) != (mode == 0)) continue;
           ltjk_ctx *c = j->req.ctx;
+          const bool native = c->opts.precision == LTJK_FP64_NATIVE;
+          if ((prec == 0 && native) || (prec == 2 && !native)) continue;
           for (size_t w = 0; w < c->work.size(); ++w) {
             ClassWork &cw = *c->work[w];
             if (quartet_index(cw.la, cw.lb, cw.lc, cw.ld, 0) != q) continue;
-            int &cur = prec == 0 ? j->cur64[w] : j->cur32[w];
-            const int n = prec == 0 ? cw.n64 : cw.n32;
+            int &cur = prec != 1 ? j->cur64[w] : j->cur32[w];
+            const int n = prec != 1 ? cw.n64 : cw.n32;
             if (cur >= n) continue;
             const int take = std::min(step_items, n - cur);
             prog = &ps->progs[quartet_index(cw.la, cw.lb, cw.lc, cw.ld, mode)];
             JobDesc &D = T.j[T.njobs++];
             D.B = c->basis();
             D.a = j->a;
-            D.items = (prec == 0 ? cw.items64.as<WorkItem>() : cw.items32.as<WorkItem>()) + cur;
+            D.items = (prec != 1 ? cw.items64.as<WorkItem>() : cw.items32.as<WorkItem>()) + cur;
             D.nitems = take;
             D.first = T.total;
             T.total += take;
@@ -244,17 +251,10 @@ void ltjk_service::run() {
       j->cur32.assign(c->work.size(), 0);
       JKArgs a{};
       if (j->req.kind == LTJK_REQ_JK) {
-        const bool mixed = c->opts.precision == LTJK_MIXED;
-        double *Dq = mem, *Sq = Dq + n, *Jq = Sq + n, *Kq = Jq + n;
-        float *D32 = mixed ? reinterpret_cast<float *>(Kq + n) : nullptr;
-        float *S32 = mixed ? D32 + n : nullptr;
-        to_qinner<<<blocks, 256, 0, st>>>(j->req.D, Dq, Sq, D32, S32, j->req.n, c->nao);
-        cudaMemsetAsync(Jq, 0, 2 * n * sizeof(double), st);
-        a.D = Dq; a.S = Sq; a.D32 = D32; a.S32 = S32;
-        a.J = j->req.J ? Jq : nullptr;
-        a.K = j->req.K ? Kq : nullptr;
-        j->Jq = Jq;
-        j->Kq = Kq;
+        a = jk_prologue(c, j->req.D, mem, j->req.n, j->req.J != nullptr, j->req.K != nullptr, st);
+        j->Jq = mem + 2 * n;
+        j->Kq = mem + 3 * n;
+        launches -= 1;  // counted below with the others
       } else {
         double *Pq = mem, *Qq = Pq + n;
         to_qinner<<<blocks, 256, 0, st>>>(j->req.P, Pq, nullptr, nullptr, nullptr, j->req.n, c->nao);
