@@ -136,6 +136,10 @@ typedef struct {
    screening, cf. the paper's Sect. "Cost" and its screening discussion).
    Synchronous.  *out receives the context. */
 int ltjk_context_create(const ltjk_basis *basis, const ltjk_opts *opts, ltjk_ctx **out);
+/* Release a context.  Work that uses it must have completed: synchronise the
+   streams it was used on (or wait for its service requests) first.  Device
+   memory of the library is stream-ordered (cudaMallocAsync/cudaFreeAsync), so
+   creating and destroying contexts never synchronises the whole device. */
 int ltjk_context_destroy(ltjk_ctx *ctx);
 int ltjk_nao(const ltjk_ctx *ctx, int *nao);
 int ltjk_context_stats(const ltjk_ctx *ctx, ltjk_ctx_stats *out);

@@ -36,19 +36,22 @@ constexpr int kSmemBudget = 200 * 1024;  // bytes of shared memory per CTA we pl
 constexpr int kMaxSmem = 227 * 1024;
 constexpr double kPrimPairDrop = 1e-18;  // drop primitive pair iff K_AB |c_a c_b| below this
 
-// Device buffer owned by a context.
+// Device buffer owned by a context.  Stream-ordered allocation
+// (cudaMallocAsync / cudaFreeAsync on the given stream, default: the legacy
+// stream) never synchronises the whole device, so contexts can be created and
+// destroyed while other work (another request, the service) runs.
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
   ~DevBuf() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, 0);
   }
-  int alloc(size_t n) {
-    if (p) cudaFree(p);
+  int alloc(size_t n, cudaStream_t st = 0) {
+    if (p) cudaFreeAsync(p, st);
     p = nullptr;
     bytes = 0;
     if (n == 0) return LTJK_OK;
-    cudaError_t e = cudaMalloc(&p, n);
+    cudaError_t e = cudaMallocAsync(&p, n, st);
     if (e != cudaSuccess) {
       p = nullptr;
       return set_error(LTJK_ENOMEM, "cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
@@ -257,12 +260,12 @@ struct ltjk_ctx {
     B.nao = nao;
     return B;
   }
-  int ensure_scratch(size_t bytes) {
+  // Grow the scratch buffer, ordered on the calling stream: the old buffer is
+  // released after the work already queued on `st` (calls on one context are
+  // ordered on one stream by contract).
+  int ensure_scratch(size_t bytes, cudaStream_t st) {
     if (scratch.bytes >= bytes) return LTJK_OK;
-    // the previous contents are dead: callers order their use on one stream and
-    // the old buffer is released only after the device is idle
-    CUDA_TRY(cudaDeviceSynchronize());
-    return scratch.alloc(bytes + bytes / 4);
+    return scratch.alloc(bytes + bytes / 4, st);
   }
 };
 
@@ -712,7 +715,10 @@ int ltjk_context_create(const ltjk_basis *bs, const ltjk_opts *opts, ltjk_ctx **
 int ltjk_context_destroy(ltjk_ctx *ctx) {
   if (!ctx) return set_error(LTJK_EINVAL, "context_destroy: null context");
   cudaSetDevice(ctx->device);
-  cudaDeviceSynchronize();
+  // the context's own streams; work the caller queued on its streams must be
+  // complete (or ordered before the legacy stream) by contract
+  for (int k = 0; k < kSideStreams; ++k)
+    if (ctx->side[k]) cudaStreamSynchronize(ctx->side[k]);
   delete ctx;
   return LTJK_OK;
 }
@@ -761,7 +767,7 @@ int ltjk_jk_build(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *
   CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t n = (size_t)ctx->nao * ctx->nao * ndens;
-  int rc = ctx->ensure_scratch(jk_scratch_bytes(ctx, ndens));
+  int rc = ctx->ensure_scratch(jk_scratch_bytes(ctx, ndens), st);
   if (rc) return rc;
   const JKArgs a = jk_prologue(ctx, D, ctx->scratch.p, ndens, J != nullptr, K != nullptr, st);
   CUDA_TRY(cudaGetLastError());
@@ -780,7 +786,7 @@ int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, do
   CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t NN = (size_t)ctx->nao * ctx->nao, n = NN * nterms;
-  int rc = ctx->ensure_scratch(2 * n * sizeof(double));
+  int rc = ctx->ensure_scratch(2 * n * sizeof(double), st);
   if (rc) return rc;
   double *Pq = ctx->scratch.as<double>(), *Qq = Pq + n;
   const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
@@ -812,9 +818,10 @@ int ltjk_pseudo_densities(ltjk_ctx *ctx, int nocc, int nvir, const double *C_occ
   const int N = ctx->nao, nq = nlap * npair;
   const size_t ny = (size_t)nq * nocc * nvir, nz = (size_t)nq * nocc * N;
   int rc;
-  if (ctx->d_t.bytes < sizeof(double) * nlap && (rc = ctx->d_t.alloc(sizeof(double) * 64 * ((nlap + 63) / 64))))
+  if (ctx->d_t.bytes < sizeof(double) * nlap &&
+      (rc = ctx->d_t.alloc(sizeof(double) * 64 * ((nlap + 63) / 64), st)))
     return rc;
-  if ((rc = ctx->ensure_scratch((ny + nz) * sizeof(double)))) return rc;
+  if ((rc = ctx->ensure_scratch((ny + nz) * sizeof(double), st))) return rc;
   double *Y = ctx->scratch.as<double>(), *Z = Y + ny;
   CUDA_TRY(cudaMemcpyAsync(ctx->d_t.p, t_host, sizeof(double) * nlap, cudaMemcpyHostToDevice, st));
   scale_amplitudes<<<(int)std::min<size_t>((ny + 255) / 256, 152 * 16), 256, 0, st>>>(

@@ -314,17 +314,27 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
       for (int L = 0; L < p.nvrr_level; ++L) {
         const int i0 = PR.levels[p.vrr_level0 + L], i1 = PR.levels[p.vrr_level0 + L + 1];
         if (active) {
-          for (int k = i0 + s; k < i1; k += S) {
-            const VrrInstr in = PR.vrr[k];
-            const int kd = in.kind, d = in.dir;
-            Real t = cf[kPAx + 3 * kd + d] * my_vrr[in.s0];
-            t = fma(cf[kWPx + 3 * kd + d], my_vrr[in.s1], t);
-            if (in.n1) {
-              const Real u = fma(-cf[kRhoZeta + kd], my_vrr[in.s3], my_vrr[in.s2]);
-              t = fma(h[kd * nh + in.n1], u, t);
-            }
-            if (in.n2) t = fma(h[2 * nh + in.n2], my_vrr[in.s4], t);
-            my_vrr[in.tgt] = t;
+          // two independent steps per lane per iteration: every source of both
+          // is read before either target is written (steps of one level never
+          // read each other), so the two dependency chains overlap
+          for (int k = i0 + s; k < i1; k += 2 * S) {
+            const bool two = k + S < i1;
+            const VrrInstr ia = PR.vrr[k];
+            const VrrInstr ib = PR.vrr[two ? k + S : k];
+            const Real a0 = my_vrr[ia.s0], a1 = my_vrr[ia.s1], a2 = my_vrr[ia.s2], a3 = my_vrr[ia.s3],
+                       a4 = my_vrr[ia.s4];
+            const Real b0 = my_vrr[ib.s0], b1 = my_vrr[ib.s1], b2 = my_vrr[ib.s2], b3 = my_vrr[ib.s3],
+                       b4 = my_vrr[ib.s4];
+            Real ta = cf[kPAx + 3 * ia.kind + ia.dir] * a0;
+            Real tb = cf[kPAx + 3 * ib.kind + ib.dir] * b0;
+            ta = fma(cf[kWPx + 3 * ia.kind + ia.dir], a1, ta);
+            tb = fma(cf[kWPx + 3 * ib.kind + ib.dir], b1, tb);
+            if (ia.n1) ta = fma(h[ia.kind * nh + ia.n1], fma(-cf[kRhoZeta + ia.kind], a3, a2), ta);
+            if (ib.n1) tb = fma(h[ib.kind * nh + ib.n1], fma(-cf[kRhoZeta + ib.kind], b3, b2), tb);
+            if (ia.n2) ta = fma(h[2 * nh + ia.n2], a4, ta);
+            if (ib.n2) tb = fma(h[2 * nh + ib.n2], b4, tb);
+            my_vrr[ia.tgt] = ta;
+            if (two) my_vrr[ib.tgt] = tb;
           }
         }
         __syncwarp();
@@ -369,10 +379,16 @@ __device__ Real *hrr_tile(const DevBasis &B, const DevProgs &PR, const ClassProg
   }
   for (int L = 0; L < T.nhrr_level; ++L) {
     const int i0 = PR.levels[T.hrr_level0 + L], i1 = PR.levels[T.hrr_level0 + L + 1];
-    for (int k = i0 + lane; k < i1; k += 32) {
-      const HrrInstr in = PR.hrr[k];
-      Real coef = in.kind < 2 ? X[in.kind][in.dir] : -Real(in.dir);
-      acc0[in.tgt] = fma(coef, acc0[in.s1], acc0[in.s0]);
+    for (int k = i0 + lane; k < i1; k += 64) {  // two independent steps per lane
+      const bool two = k + 32 < i1;
+      const HrrInstr ia = PR.hrr[k];
+      const HrrInstr ib = PR.hrr[two ? k + 32 : k];
+      const Real ca = ia.kind < 2 ? X[ia.kind][ia.dir] : -Real(ia.dir);
+      const Real cb = ib.kind < 2 ? X[ib.kind][ib.dir] : -Real(ib.dir);
+      const Real ta = fma(ca, acc0[ia.s1], acc0[ia.s0]);
+      const Real tb = fma(cb, acc0[ib.s1], acc0[ib.s0]);
+      acc0[ia.tgt] = ta;
+      if (two) acc0[ib.tgt] = tb;
     }
     __syncwarp();
   }
@@ -417,16 +433,40 @@ __device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], cons
     double *T = P.isJ ? a.J : a.K;
     const int nr = n[P.orow], nc = n[P.ocol], nu = n[P.srow], nv = n[P.scol];
     const int sr = str[P.orow], sc = str[P.ocol], su = str[P.srow], sv = str[P.scol];
-    const int items = nr * nc * nd;
-    for (int t = lane; t < items; t += 32) {
-      const int q = t % nd, o = t / nd;
-      const int x = o / nc, y = o % nc;
-      const Real *Ib = I + x * sr + y * sc;
-      const Real *Mb = M + ((size_t)off[P.srow] * N + off[P.scol]) * nd + q;
-      Real acc = zero_real<Real>();
-      for (int u = 0; u < nu; ++u)
-        for (int v = 0; v < nv; ++v) acc = fma(Ib[u * su + v * sv], ldg(Mb + ((size_t)u * N + v) * nd), acc);
-      atomicAdd(T + ((size_t)(off[P.orow] + x) * N + off[P.ocol] + y) * nd + q, to_double(acc));
+    const Real *Mblk = M + ((size_t)off[P.srow] * N + off[P.scol]) * nd;
+    const size_t mrow = (size_t)N * nd;  // stride of one AO row in the q-innermost layout
+    // output coordinates are warp-uniform; lanes run over densities; four
+    // outputs per pass share each density load and give four independent
+    // accumulation chains
+    const int nout = nr * nc;
+    for (int o0 = 0; o0 < nout; o0 += 4) {
+      const Real *Ib[4];
+      double *To[4];
+      const int cnt = min(4, nout - o0);
+      for (int j = 0; j < 4; ++j) {
+        const int o = o0 + (j < cnt ? j : 0), x = o / nc, y = o - (o / nc) * nc;
+        Ib[j] = I + x * sr + y * sc;
+        To[j] = T + ((size_t)(off[P.orow] + x) * N + off[P.ocol] + y) * nd;
+      }
+      for (int q = lane; q < nd; q += 32) {
+        Real acc0 = zero_real<Real>(), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+        const Real *Mu = Mblk + q;
+        for (int u = 0; u < nu; ++u, Mu += mrow) {
+          const int iu = u * su;
+          for (int v = 0; v < nv; ++v) {
+            const Real m = ldg(Mu + (size_t)v * nd);
+            const int iv = iu + v * sv;
+            acc0 = fma(Ib[0][iv], m, acc0);
+            acc1 = fma(Ib[1][iv], m, acc1);
+            acc2 = fma(Ib[2][iv], m, acc2);
+            acc3 = fma(Ib[3][iv], m, acc3);
+          }
+        }
+        atomicAdd(To[0] + q, to_double(acc0));
+        if (cnt > 1) atomicAdd(To[1] + q, to_double(acc1));
+        if (cnt > 2) atomicAdd(To[2] + q, to_double(acc2));
+        if (cnt > 3) atomicAdd(To[3] + q, to_double(acc3));
+      }
     }
   }
 }

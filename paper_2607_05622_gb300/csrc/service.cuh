@@ -79,6 +79,8 @@ double now_s() {
 struct ltjk_service {
   int device = 0;
   cudaStream_t st = nullptr;
+  cudaStream_t side[kSideStreams] = {};  // class launches of a step run concurrently
+  cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
   Arena arena;
   std::thread thr;
   std::mutex mu;
@@ -142,6 +144,8 @@ int ltjk_service::step(std::vector<SvcJob *> &run) {
   const ProgramSet *ps;
   if (program_set(&ps)) return -1;
   int nl = 0;
+  cudaEventRecord(fork_ev, st);
+  for (int k = 0; k < kSideStreams; ++k) cudaStreamWaitEvent(side[k], fork_ev, 0);
   for (int mode = 0; mode < 2; ++mode)
     for (int prec = 0; prec < 3; ++prec)
       for (int q = 0; q < kNumPairClass * kNumPairClass; ++q) {
@@ -152,6 +156,7 @@ int ltjk_service::step(std::vector<SvcJob *> &run) {
         auto flush = [&]() {
           if (T.total == 0) return;
           const DevProgs &PR = run[0]->req.ctx->progs;
+          cudaStream_t st = side[nl % kSideStreams];
           if (mode == 0) {
             if (prec == 0)
               launch_class<dflt, kJK>(PR, make_launch(*prog, sizeof(dflt)), T, st);
@@ -197,6 +202,10 @@ int ltjk_service::step(std::vector<SvcJob *> &run) {
         }
         flush();
       }
+  for (int k = 0; k < kSideStreams; ++k) {
+    cudaEventRecord(join_ev[k], side[k]);
+    cudaStreamWaitEvent(st, join_ev[k], 0);
+  }
   return nl;
 }
 
@@ -372,6 +381,11 @@ int ltjk_service_create(size_t hbm_budget_bytes, int device, ltjk_service **out)
   s->arena.size = hbm_budget_bytes;
   s->arena.free_[0] = hbm_budget_bytes;
   e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+  for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&s->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join_ev[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaFree(p);
     return set_error(LTJK_ECUDA, "stream: %s", cudaGetErrorString(e));
@@ -504,6 +518,11 @@ int ltjk_service_destroy(ltjk_service *s) {
   for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
   for (auto &kv : s->jobs)
     if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+  for (int k = 0; k < kSideStreams; ++k) {
+    if (s->side[k]) cudaStreamDestroy(s->side[k]);
+    if (s->join_ev[k]) cudaEventDestroy(s->join_ev[k]);
+  }
+  if (s->fork_ev) cudaEventDestroy(s->fork_ev);
   cudaStreamDestroy(s->st);
   cudaFree(s->arena.base);
   delete s;

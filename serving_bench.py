@@ -1,0 +1,183 @@
+"""Serving benchmark: a Poisson stream of J/K and gradient requests on one GB300.
+
+Request stream (paper_2607_05622_gb300.workloads.serving_requests): chain
+molecules with AO counts log-uniform in [25, 730], 8-16 Laplace points, 1-3
+transition pairs, 70 % J/K builds and 30 % gradients (8 terms), mixed
+precision, admitted under a 150 GB HBM budget by the continuous-batching
+service.  Reported against the same request list run one at a time in plain
+IEEE FP64 on the same GPU:
+
+  1. sequential FP64 pass: per request, context + pseudo-densities + build,
+     service time, and 4096 sampled result elements kept as the reference;
+  2. mixed-precision single-request pass (service time only) to measure the
+     capacity; the arrival rate is set to 0.8 x that capacity;
+  3. the stream replayed in real time into the service; latency = completion
+     time - arrival time (context creation and density formation included).
+
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2607_05622_gb300 import workloads as W  # noqa: E402
+
+
+def prepare(L, req, precision, dev, torch):
+    """Context and device inputs of one request (timed as part of its service)."""
+    inp = W.request_inputs(req)
+    mol = req["mol"]
+    ctx = L.Context(mol, schwarz_tau=1e-12, mixed_tau=1e-6, precision=precision)
+    if req["kind"] == "jk":
+        xmin = 2.0 * (inp["eps_vir"].min() - inp["eps_occ"].max())
+        xmax = 2.0 * (inp["eps_vir"].max() - inp["eps_occ"].min())
+        t, _, _ = L.laplace_quadrature(xmin, xmax, req["nlap"])
+        C = inp["C"]
+        Co = torch.from_numpy(np.ascontiguousarray(C[:, :inp["nocc"]])).to(dev)
+        Cv = torch.from_numpy(np.ascontiguousarray(C[:, inp["nocc"]:])).to(dev)
+        D = ctx.pseudo_densities(Co, Cv, torch.from_numpy(inp["eps_occ"]).to(dev),
+                                 torch.from_numpy(inp["eps_vir"]).to(dev),
+                                 torch.from_numpy(np.ascontiguousarray(inp["X"])).to(dev), t)
+        return ctx, {"D": D}
+    P = torch.from_numpy(inp["P"]).to(dev)
+    Q = torch.from_numpy(inp["Q"]).to(dev)
+    return ctx, {"P": P, "Q": Q}
+
+
+def sample_index(n, k, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, n, size=min(k, n))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--nao-max", type=int, default=730)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--load", type=float, default=0.8)
+    args = ap.parse_args()
+    import torch
+    from paper_2607_05622_gb300 import ltjk as L
+    dev = torch.device("cuda:0")
+    reqs = W.serving_requests(args.requests, seed=5, nao_hi=args.nao_max, rate_hz=1.0)
+    ref = []
+    seq_fp64 = []
+    # 1. sequential plain FP64
+    for r in reqs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx, inp = prepare(L, r, L.FP64_NATIVE, dev, torch)
+        if r["kind"] == "jk":
+            J, K = ctx.jk_build(inp["D"])
+            torch.cuda.synchronize()
+            idx = sample_index(J.numel(), 4096, r["seed"])
+            ref.append((J.flatten()[idx].cpu().numpy(), K.flatten()[idx].cpu().numpy(),
+                        float(J.abs().max()), float(K.abs().max()), idx))
+        else:
+            g = ctx.jk_grad(inp["P"], inp["Q"], 1.0, 0.0)
+            torch.cuda.synchronize()
+            ref.append((g.cpu().numpy(),))
+        seq_fp64.append(time.perf_counter() - t0)
+        ctx.close()
+        del inp
+    # 2. mixed single-request service times (capacity)
+    seq_mixed = []
+    for r in reqs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx, inp = prepare(L, r, L.MIXED, dev, torch)
+        if r["kind"] == "jk":
+            ctx.jk_build(inp["D"])
+        else:
+            ctx.jk_grad(inp["P"], inp["Q"], 1.0, 0.0)
+        torch.cuda.synchronize()
+        seq_mixed.append(time.perf_counter() - t0)
+        ctx.close()
+        del inp
+    capacity = len(reqs) / sum(seq_mixed)
+    rate = args.load * capacity
+    # arrival times rescaled to the chosen rate (same Poisson draws)
+    base = np.array([r["arrival"] for r in reqs])
+    arrivals = base * (1.0 / rate) / (base[-1] / len(reqs))
+    # 3. served stream
+    svc = L.Service(int(args.budget_gb * (1 << 30)))
+    pending = {}
+    lat, errs_j, errs_k, errs_g = [], [], [], []
+    t_start = time.perf_counter()
+    k = 0
+
+    def harvest(block=False):
+        for tk in list(pending):
+            i, ctx, inp, out, t_arr = pending[tk]
+            done, rc = svc.poll(tk)
+            if not done:
+                continue
+            t_done = time.perf_counter() - t_start
+            L._check(rc)
+            lat.append(t_done - t_arr)
+            if reqs[i]["kind"] == "jk":
+                J, K = out
+                rj, rk, mj, mk, idx = ref[i]
+                errs_j.append(float(np.abs(J.flatten()[idx].cpu().numpy() - rj).max()) / mj)
+                errs_k.append(float(np.abs(K.flatten()[idx].cpu().numpy() - rk).max()) / mk)
+            else:
+                g = out[0].cpu().numpy()
+                errs_g.append(float(np.abs(g - ref[i][0]).max() / np.abs(ref[i][0]).max()))
+            ctx.close()
+            del pending[tk]
+
+    while k < len(reqs) or pending:
+        now = time.perf_counter() - t_start
+        if k < len(reqs) and now >= arrivals[k]:
+            r = reqs[k]
+            ctx, inp = prepare(L, r, L.MIXED, dev, torch)
+            if r["kind"] == "jk":
+                tk, J, K = svc.submit_jk(ctx, inp["D"])
+                pending[tk] = (k, ctx, inp, (J, K), arrivals[k])
+            else:
+                tk, g = svc.submit_grad(ctx, inp["P"], inp["Q"], 1.0, 0.0)
+                pending[tk] = (k, ctx, inp, (g,), arrivals[k])
+            k += 1
+            continue
+        harvest()
+        time.sleep(0.0005)
+    span = time.perf_counter() - t_start
+    st = svc.stats()
+    svc.close()
+    lat_ms = sorted(1e3 * x for x in lat)
+    pct = lambda p: lat_ms[min(len(lat_ms) - 1, int(round(p * (len(lat_ms) - 1))))]  # noqa: E731
+    nao = [r["mol"].nao for r in reqs]
+    out = {
+        "metric": "serving: p50/p99 latency and throughput, mixed precision, continuous batching",
+        "requests": len(reqs), "jk": sum(r["kind"] == "jk" for r in reqs),
+        "grad": sum(r["kind"] == "grad" for r in reqs),
+        "nao_min": min(nao), "nao_median": int(np.median(nao)), "nao_max": max(nao),
+        "arrival_rate_hz": rate, "offered_load": args.load,
+        "p50_ms": pct(0.5), "p99_ms": pct(0.99), "mean_ms": statistics.mean(lat_ms),
+        "throughput_rps": len(reqs) / span, "span_s": span,
+        "sequential_fp64": {"throughput_rps": len(reqs) / sum(seq_fp64),
+                            "p50_service_ms": 1e3 * float(np.median(seq_fp64)),
+                            "total_s": sum(seq_fp64)},
+        "sequential_mixed": {"throughput_rps": capacity, "total_s": sum(seq_mixed)},
+        "error_vs_fp64": {"J_max_rel_to_max": max(errs_j) if errs_j else None,
+                          "K_max_rel_to_max": max(errs_k) if errs_k else None,
+                          "grad_max_rel_to_max": max(errs_g) if errs_g else None,
+                          "how": "4096 sampled elements per J/K result, full gradient"},
+        "service": {k2: st[k2] for k2 in ("steps", "launches", "bytes_peak", "budget", "completed")},
+        "budget_gb": args.budget_gb,
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
