@@ -288,19 +288,33 @@ def run_gpu(args, world, rank, local):
         del c64
     # roofline of the dominant kernel (the J/K quartet kernels of one build)
     clocks = clk.summary(local)
-    sm_mhz = clocks["sm_mhz"] or 1965.0
     jk_s = statistics.mean(jk_ms) / 1e3
     dig = 20.0 * st["cart_integrals_kept"] * nd
     flops = st["eri_flops_per_build"] + dig
+    flops64 = st["eri_flops_fp64"] + 20.0 * st["cart_integrals_fp64"] * nd
     pk = alu_peaks(2070.0)
-    peak = pk["fp64_tflops"] if prec == ltjk.FP64_NATIVE else pk["fp32_tflops"]
-    roof = {"bound": "alu",
-            "pipe": "fp64" if prec == ltjk.FP64_NATIVE else
-                    "fp32 (double-float / FP32 recurrences and digestion) + fp64 (Boys, setup, accumulation)",
+    # FP64-class arithmetic as double-float on the FP32 pipe: one double-float
+    # FMA (2 flops) costs 15 FP32 instructions, so its peak is 2/15 of the FP32
+    # instruction rate; mixed precision weights the double-float and FP32 peaks
+    # by the share of algorithmic flops in each.
+    df_peak = pk["fp32_tflops"] / 2.0 * 2.0 / 15.0
+    if prec == ltjk.FP64_NATIVE:
+        peak, pipe = pk["fp64_tflops"], "fp64 FMA"
+        src = "152 SMs x 2 FP64 FMA/clk x 2070 MHz"
+    elif prec == ltjk.FP64:
+        peak, pipe = df_peak, "fp32 FMA pipe running double-float (15 FP32 instructions per FMA)"
+        src = "152 SMs x 128 FP32 lanes x 2070 MHz x 2 flops / 15 instructions"
+    else:
+        f64 = flops64 / flops
+        peak = 1.0 / (f64 / df_peak + (1.0 - f64) / pk["fp32_tflops"])
+        pipe = f"fp32 FMA pipe: {100 * f64:.0f}% of the flops double-float, the rest FP32"
+        src = ("harmonic mix of the double-float peak (FP32 rate x 2/15) and the FP32 FMA peak "
+               "(152 x 128 x 2 x 2070 MHz) by flop share")
+    roof = {"bound": "alu", "pipe": pipe,
             "achieved": flops / jk_s / 1e12, "peak": peak, "unit": "TFLOP/s",
             "frac": flops / jk_s / 1e12 / peak, "traffic": None,
-            "algorithmic_flops_per_build": flops,
-            "peak_source": "unit counts x 2070 MHz max SM clock (152 SMs; 128 FP32 or 2 FP64 FMA/clk/SM)"}
+            "algorithmic_flops_per_build": flops, "peak_source": src,
+            "fp32_pipe_peak_tflops": pk["fp32_tflops"], "fp64_pipe_peak_tflops": pk["fp64_tflops"]}
     if rank != 0:
         return
     cpu = None

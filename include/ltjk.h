@@ -128,6 +128,8 @@ typedef struct {
   int64_t cart_integrals_kept;/* contracted Cartesian integrals over the kept quartets */
   double eri_flops_per_build; /* recurrence flop model over the kept quartets */
   size_t device_bytes;        /* device memory held by the context */
+  double eri_flops_fp64;      /* part of eri_flops_per_build in FP64-class quartets */
+  int64_t cart_integrals_fp64;/* part of cart_integrals_kept in FP64-class quartets */
 } ltjk_ctx_stats;
 
 /* Create a context: normalises the basis, builds every shell pair and its

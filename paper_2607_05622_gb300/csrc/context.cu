@@ -401,6 +401,8 @@ int build_work(ltjk_ctx &c) {
   c.stats.prim_quartets_kept = 0;
   c.stats.cart_integrals_kept = 0;
   c.stats.eri_flops_per_build = 0;
+  c.stats.eri_flops_fp64 = 0;
+  c.stats.cart_integrals_fp64 = 0;
   std::vector<int> npp_host(c.npairs);
   {
     // primitive pair counts are needed for the statistics
@@ -454,12 +456,17 @@ int build_work(ltjk_ctx &c) {
         tot32 += nkeep - n64;
         c.stats.quartets_kept += nkeep;
         c.stats.quartets_fp64 += n64;
-        long long npq = 0;
-        for (int j = 0; j < nkeep; ++j) npq += (long long)npp_host[i] * npp_host[yb + j];
+        long long npq = 0, npq64 = 0;
+        for (int j = 0; j < nkeep; ++j) {
+          npq += (long long)npp_host[i] * npp_host[yb + j];
+          if (j == n64 - 1) npq64 = npq;
+        }
         c.stats.prim_quartets_kept += npq;
-        c.stats.cart_integrals_kept +=
-            (long long)nkeep * ncart(cw->la) * ncart(cw->lb) * ncart(cw->lc) * ncart(cw->ld);
+        const long long nint = (long long)ncart(cw->la) * ncart(cw->lb) * ncart(cw->lc) * ncart(cw->ld);
+        c.stats.cart_integrals_kept += (long long)nkeep * nint;
+        c.stats.cart_integrals_fp64 += (long long)n64 * nint;
         c.stats.eri_flops_per_build += class_flops(p, npq);
+        if (n64 > 0) c.stats.eri_flops_fp64 += class_flops(p, npq64);
       }
       // kets per work item: small enough that a class yields at least
       // kTargetItems items (heavy classes have few quartets), at most kKetChunk

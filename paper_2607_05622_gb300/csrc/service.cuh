@@ -144,8 +144,6 @@ int ltjk_service::step(std::vector<SvcJob *> &run) {
   const ProgramSet *ps;
   if (program_set(&ps)) return -1;
   int nl = 0;
-  cudaEventRecord(fork_ev, st);
-  for (int k = 0; k < kSideStreams; ++k) cudaStreamWaitEvent(side[k], fork_ev, 0);
   for (int mode = 0; mode < 2; ++mode)
     for (int prec = 0; prec < 3; ++prec)
       for (int q = 0; q < kNumPairClass * kNumPairClass; ++q) {
@@ -156,7 +154,10 @@ int ltjk_service::step(std::vector<SvcJob *> &run) {
         auto flush = [&]() {
           if (T.total == 0) return;
           const DevProgs &PR = run[0]->req.ctx->progs;
-          cudaStream_t st = side[nl % kSideStreams];
+          // a class always runs on the same side stream: launches of one class
+          // stay ordered, different classes overlap, and no step waits for
+          // the previous one to drain
+          cudaStream_t st = side[q % kSideStreams];
           if (mode == 0) {
             if (prec == 0)
               launch_class<dflt, kJK>(PR, make_launch(*prog, sizeof(dflt)), T, st);
@@ -202,10 +203,6 @@ int ltjk_service::step(std::vector<SvcJob *> &run) {
         }
         flush();
       }
-  for (int k = 0; k < kSideStreams; ++k) {
-    cudaEventRecord(join_ev[k], side[k]);
-    cudaStreamWaitEvent(st, join_ev[k], 0);
-  }
   return nl;
 }
 
@@ -277,6 +274,10 @@ void ltjk_service::run() {
       launches += 2;
       run_jobs.push_back(j);
     }
+    if (!admitted.empty()) {  // their layout copies (on st) precede their class launches
+      cudaEventRecord(fork_ev, st);
+      for (int k = 0; k < kSideStreams; ++k) cudaStreamWaitEvent(side[k], fork_ev, 0);
+    }
     int nl = 0;
     if (!run_jobs.empty()) nl = step(run_jobs);
     if (nl > 0) {
@@ -298,6 +299,12 @@ void ltjk_service::run() {
         if (all) to_finish.push_back(j);
       }
     }
+    if (!to_finish.empty()) {  // every class launch issued so far precedes the epilogues
+      for (int k = 0; k < kSideStreams; ++k) {
+        cudaEventRecord(join_ev[k], side[k]);
+        cudaStreamWaitEvent(st, join_ev[k], 0);
+      }
+    }
     for (SvcJob *j : to_finish) {
       if (!j->cancel_req && j->req.kind == LTJK_REQ_JK) {
         ltjk_ctx *c = j->req.ctx;
@@ -312,11 +319,13 @@ void ltjk_service::run() {
       std::lock_guard<std::mutex> g(mu);
       j->state = kDraining;
     }
-    // keep the host at most two steps ahead of the device
-    cudaEvent_t se = get_event();
-    cudaEventRecord(se, st);
-    inflight.push_back(se);
-    while (inflight.size() > 2) {
+    // keep the host a bounded number of steps ahead of the device
+    if (nl > 0) {
+      cudaEvent_t se = get_event();
+      cudaEventRecord(se, side[steps % kSideStreams]);
+      inflight.push_back(se);
+    }
+    while (inflight.size() > 2 * kSideStreams) {
       wait_event(inflight.front(), 600.0);
       put_event(inflight.front());
       inflight.pop_front();

@@ -44,7 +44,8 @@ class CtxStats(ctypes.Structure):
                 ("quartets_total", ctypes.c_int64), ("quartets_kept", ctypes.c_int64),
                 ("quartets_fp64", ctypes.c_int64), ("prim_quartets_kept", ctypes.c_int64),
                 ("cart_integrals_kept", ctypes.c_int64), ("eri_flops_per_build", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("eri_flops_fp64", ctypes.c_double),
+                ("cart_integrals_fp64", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

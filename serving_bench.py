@@ -11,8 +11,10 @@ IEEE FP64 on the same GPU:
      service time, and 4096 sampled result elements kept as the reference;
   2. mixed-precision single-request pass (service time only) to measure the
      capacity; the arrival rate is set to 0.8 x that capacity;
-  3. the stream replayed in real time into the service; latency = completion
-     time - arrival time (context creation and density formation included).
+  3. the stream replayed in real time into the service by a pool of frontend
+     threads that build each request's context and densities on arrival;
+     latency = completion time - arrival time (context creation and density
+     formation included).
 
 Prints one JSON line.
 """
@@ -65,6 +67,7 @@ def main():
     ap.add_argument("--nao-max", type=int, default=730)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--frontend-threads", type=int, default=4)
     args = ap.parse_args()
     import torch
     from paper_2607_05622_gb300 import ltjk as L
@@ -109,16 +112,38 @@ def main():
     # arrival times rescaled to the chosen rate (same Poisson draws)
     base = np.array([r["arrival"] for r in reqs])
     arrivals = base * (1.0 / rate) / (base[-1] / len(reqs))
-    # 3. served stream
+    # 3. served stream: a pool of host threads (a serving frontend) builds each
+    # request's context and densities when it arrives and submits it; the main
+    # thread collects completions.  Latency = completion - arrival.
+    import concurrent.futures as cf
+    import threading
     svc = L.Service(int(args.budget_gb * (1 << 30)))
     pending = {}
+    lock = threading.Lock()
     lat, errs_j, errs_k, errs_g = [], [], [], []
     t_start = time.perf_counter()
-    k = 0
 
-    def harvest(block=False):
-        for tk in list(pending):
-            i, ctx, inp, out, t_arr = pending[tk]
+    def arrive(i):
+        dt = arrivals[i] - (time.perf_counter() - t_start)
+        if dt > 0:
+            time.sleep(dt)
+        r = reqs[i]
+        s_ = torch.cuda.Stream()
+        with torch.cuda.stream(s_):
+            ctx, inp = prepare(L, r, L.MIXED, dev, torch)
+            if r["kind"] == "jk":
+                tk, J, K = svc.submit_jk(ctx, inp["D"])
+                out = (J, K)
+            else:
+                tk, g = svc.submit_grad(ctx, inp["P"], inp["Q"], 1.0, 0.0)
+                out = (g,)
+        with lock:
+            pending[tk] = (i, ctx, inp, out, arrivals[i])
+
+    def harvest():
+        with lock:
+            items = list(pending.items())
+        for tk, (i, ctx, inp, out, t_arr) in items:
             done, rc = svc.poll(tk)
             if not done:
                 continue
@@ -134,23 +159,17 @@ def main():
                 g = out[0].cpu().numpy()
                 errs_g.append(float(np.abs(g - ref[i][0]).max() / np.abs(ref[i][0]).max()))
             ctx.close()
-            del pending[tk]
+            with lock:
+                del pending[tk]
 
-    while k < len(reqs) or pending:
-        now = time.perf_counter() - t_start
-        if k < len(reqs) and now >= arrivals[k]:
-            r = reqs[k]
-            ctx, inp = prepare(L, r, L.MIXED, dev, torch)
-            if r["kind"] == "jk":
-                tk, J, K = svc.submit_jk(ctx, inp["D"])
-                pending[tk] = (k, ctx, inp, (J, K), arrivals[k])
-            else:
-                tk, g = svc.submit_grad(ctx, inp["P"], inp["Q"], 1.0, 0.0)
-                pending[tk] = (k, ctx, inp, (g,), arrivals[k])
-            k += 1
-            continue
-        harvest()
-        time.sleep(0.0005)
+    with cf.ThreadPoolExecutor(max_workers=args.frontend_threads) as pool:
+        futs = [pool.submit(arrive, i) for i in range(len(reqs))]
+        while len(lat) < len(reqs):
+            harvest()
+            for f in futs:
+                if f.done() and f.exception():
+                    raise f.exception()
+            time.sleep(0.001)
     span = time.perf_counter() - t_start
     st = svc.stats()
     svc.close()
@@ -174,7 +193,7 @@ def main():
                           "grad_max_rel_to_max": max(errs_g) if errs_g else None,
                           "how": "4096 sampled elements per J/K result, full gradient"},
         "service": {k2: st[k2] for k2 in ("steps", "launches", "bytes_peak", "budget", "completed")},
-        "budget_gb": args.budget_gb,
+        "budget_gb": args.budget_gb, "frontend_threads": args.frontend_threads,
     }
     print(json.dumps(out))
 
