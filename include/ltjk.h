@@ -159,6 +159,24 @@ int ltjk_schwarz(const ltjk_ctx *ctx, double *Q_host);
 int ltjk_laplace_quadrature(double xmin, double xmax, int n, double *t_host, double *w_host,
                             double *max_rel_err);
 
+/* Minimax (best uniform relative error) exponential sum for 1/x on
+   [xmin, xmax] -- the grid the paper prescribes (Eq. laplace) -- by the Remez
+   exchange started from the least-squares fit: the relative error of the
+   result equioscillates at 2n+1 points.  Host-only, synchronous.  Arguments
+   as ltjk_laplace_quadrature; *converged (nullable) is 1 when the exchange
+   levelled the error, 0 when it stopped early (the nodes returned are then
+   the least-squares ones). */
+int ltjk_laplace_minimax(double xmin, double xmax, int n, double *t_host, double *w_host,
+                         double *max_rel_err, int *converged);
+
+/* EOM excitation-energy shift of a grid (Eq. eomshift):
+   w_shifted[q] = w[q] exp(omega t[q]), so that sum_q w_shifted[q] exp(-t[q] D)
+   approximates 1/(D - omega) with the grid's relative accuracy wherever
+   D - omega lies in the fitted range (valid for omega below the smallest
+   denominator).  Host-only. */
+int ltjk_laplace_shift(int n, const double *t_host, const double *w_host, double omega,
+                       double *w_shifted_host);
+
 /* --------------------------------------------------------- pseudo-densities */
 /* D[q*npair + p] = U_q X_p V_q^T, U_q = C_occ diag(exp(+t_q eps_occ)),
    V_q = C_vir diag(exp(-t_q eps_vir)) (Eq. scaledcoeff; Eq. aodensk with the

@@ -316,3 +316,62 @@ def denominator_sums(I, C_occ, C_vir, eps_occ, eps_vir, X):
     tJ = XX * ovov / den
     tK = XX * oovv.transpose(0, 2, 1, 3) / den
     return float(tJ.sum()), float(tK.sum()), float(np.abs(tJ).sum()), float(np.abs(tK).sum())
+
+
+# --------------------------------------------- minimax quadrature (Eq. laplace)
+def _rel_err_fn(t, w, x):
+    return 1.0 - x * (np.exp(-np.outer(x, t)) @ w)
+
+
+def _alternation_points(t, w, R, n, ngrid=40000):
+    """The 2n+1 extrema of e(x) = 1 - x sum w e^{-t x} on [1, R] with alternating
+    signs: split a fine log grid at the sign changes of e and take the point of
+    largest |e| in every piece."""
+    x = np.geomspace(1.0, R, ngrid)
+    e = _rel_err_fn(t, w, x)
+    sgn = np.sign(e)
+    cuts = np.nonzero(sgn[1:] != sgn[:-1])[0] + 1
+    pieces = np.split(np.arange(ngrid), cuts)
+    pts = np.array([x[p[np.argmax(np.abs(e[p]))]] for p in pieces])
+    return pts, e
+
+
+def laplace_minimax(xmin: float, xmax: float, n: int, iters: int = 60, tol: float = 1e-6):
+    """Best uniform (minimax) relative approximation sum_q w_q exp(-t_q x) ~ 1/x
+    on [xmin, xmax], the grid the paper asks for (Eq. laplace), by the Remez
+    exchange: starting from the least-squares fit, repeatedly (1) take the 2n+1
+    alternating extrema x_i of the relative error e(x) = 1 - x sum w e^{-t x} and
+    (2) solve e(x_i) = (-1)^i E for (log t, log w, E) by Newton's method, until
+    the levelled error E equals the maximum error.  Returns (t, w, max_rel_err)."""
+    from scipy.optimize import least_squares
+
+    R = xmax / xmin
+    t, w, _ = laplace_quadrature(xmin, xmax, n)
+    t, w = t * xmin, w * xmin  # normalised problem on [1, R]
+    E = 0.0
+    for _ in range(iters):
+        pts, e = _alternation_points(t, w, R, n)
+        if len(pts) != 2 * n + 1:
+            break
+        signs = np.sign(_rel_err_fn(t, w, pts))
+        E0 = float(np.mean(np.abs(_rel_err_fn(t, w, pts))))
+
+        def eqs(th):
+            tt, ww, EE = np.exp(th[:n]), np.exp(th[n:2 * n]), th[2 * n]
+            return _rel_err_fn(tt, ww, pts) - signs * EE
+
+        th0 = np.concatenate([np.log(t), np.log(w), [E0]])
+        sol = least_squares(eqs, th0, method="lm", xtol=1e-15, ftol=1e-15, gtol=1e-15)
+        t, w, E = np.exp(sol.x[:n]), np.exp(sol.x[n:2 * n]), abs(sol.x[2 * n])
+        emax = float(np.max(np.abs(_rel_err_fn(t, w, np.geomspace(1.0, R, 40000)))))
+        if emax <= E * (1 + tol):
+            break
+    order = np.argsort(t)
+    t, w = t[order] / xmin, w[order] / xmin
+    return t, w, laplace_error(t, w, xmin, xmax)
+
+
+def laplace_shift(t, w, omega):
+    """EOM-shifted weights w_q e^{omega t_q} (Eq. eomshift): sum_q w~_q e^{-t_q D}
+    approximates 1/(D - omega) wherever D - omega lies in the fitted range."""
+    return np.asarray(w) * np.exp(omega * np.asarray(t))

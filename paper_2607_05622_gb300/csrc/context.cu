@@ -766,6 +766,19 @@ int ltjk_laplace_quadrature(double xmin, double xmax, int n, double *t_host, dou
   return laplace_quadrature(xmin, xmax, n, t_host, w_host, max_rel_err);
 }
 
+int ltjk_laplace_minimax(double xmin, double xmax, int n, double *t_host, double *w_host,
+                         double *max_rel_err, int *converged) {
+  return laplace_minimax(xmin, xmax, n, t_host, w_host, max_rel_err, converged);
+}
+
+int ltjk_laplace_shift(int n, const double *t_host, const double *w_host, double omega,
+                       double *w_shifted_host) {
+  if (n < 1 || !t_host || !w_host || !w_shifted_host || !std::isfinite(omega))
+    return set_error(LTJK_EINVAL, "laplace_shift: bad argument");
+  for (int q = 0; q < n; ++q) w_shifted_host[q] = w_host[q] * std::exp(omega * t_host[q]);
+  return LTJK_OK;
+}
+
 int ltjk_jk_build(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *K,
                   ltjk_stream stream) {
   if (!ctx || !D) return set_error(LTJK_EINVAL, "jk_build: null context or density");

@@ -389,4 +389,178 @@ int laplace_quadrature(double xmin, double xmax, int n, double *t_out, double *w
   return LTJK_OK;
 }
 
+// ------------------------------------------------ minimax (Remez exchange)
+// Best uniform relative approximation on [1, R]: the error e(x) = 1 - x sum w
+// e^{-t x} of the optimum equioscillates at 2n+1 points.  Starting from the
+// least-squares fit: (1) locate the 2n+1 alternating extrema of e on a fine
+// log grid (split at sign changes, largest |e| in each piece); (2) solve
+// e(x_i) = s_i E for (log t, log w, E) by damped Newton with Gaussian
+// elimination; repeat until the levelled E equals the maximum error.
+namespace {
+
+double rel_err(const std::vector<double> &t, const std::vector<double> &w, double x) {
+  double v = 0.0;
+  for (size_t q = 0; q < t.size(); ++q) v += w[q] * std::exp(-t[q] * x);
+  return 1.0 - x * v;
+}
+
+bool alternation(const std::vector<double> &t, const std::vector<double> &w, double R, int n,
+                 std::vector<double> &pts, std::vector<double> &sg, double *emax) {
+  const int ng = 20000;
+  const double lr = std::log(R);
+  pts.clear();
+  sg.clear();
+  *emax = 0.0;
+  double best = -1.0, bx = 1.0;
+  int cur = 0;
+  for (int k = 0; k < ng; ++k) {
+    const double x = std::exp(lr * k / (ng - 1)), e = rel_err(t, w, x);
+    const int s = e > 0 ? 1 : (e < 0 ? -1 : cur);
+    *emax = std::max(*emax, std::fabs(e));
+    if (k > 0 && s != cur && cur != 0) {
+      pts.push_back(bx);
+      sg.push_back(cur);
+      best = -1.0;
+    }
+    cur = s;
+    if (std::fabs(e) > best) {
+      best = std::fabs(e);
+      bx = x;
+    }
+  }
+  pts.push_back(bx);
+  sg.push_back(cur);
+  return (int)pts.size() == 2 * n + 1;
+}
+
+bool solve_dense(int m, std::vector<double> &A, std::vector<double> &b) {
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (std::fabs(A[(size_t)r * m + c]) > std::fabs(A[(size_t)piv * m + c])) piv = r;
+    if (A[(size_t)piv * m + c] == 0.0) return false;
+    if (piv != c) {
+      for (int k = 0; k < m; ++k) std::swap(A[(size_t)c * m + k], A[(size_t)piv * m + k]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < m; ++r) {
+      const double f = A[(size_t)r * m + c] / A[(size_t)c * m + c];
+      if (f == 0.0) continue;
+      for (int k = c; k < m; ++k) A[(size_t)r * m + k] -= f * A[(size_t)c * m + k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = m - 1; r >= 0; --r) {
+    double v = b[r];
+    for (int k = r + 1; k < m; ++k) v -= A[(size_t)r * m + k] * b[k];
+    b[r] = v / A[(size_t)r * m + r];
+  }
+  return true;
+}
+
+// Remez on [1, R] from (t, w); returns false (inputs untouched) on failure.
+bool remez(double R, int n, std::vector<double> &t, std::vector<double> &w) {
+  std::vector<double> tt = t, ww = w, pts, sg;
+  double emax = 0.0, E = 0.0;
+  bool ok = false;
+  for (int it = 0; it < 60; ++it) {
+    if (!alternation(tt, ww, R, n, pts, sg, &emax)) break;
+    E = 0.0;
+    for (int i = 0; i <= 2 * n; ++i) E += std::fabs(rel_err(tt, ww, pts[i]));
+    E /= 2 * n + 1;
+    if (it > 0 && emax <= E * (1.0 + 1e-6)) {
+      ok = true;
+      break;
+    }
+    // Newton on F_i = e(x_i) - s_i E over theta = (log t, log w, E)
+    const int m = 2 * n + 1;
+    std::vector<double> th(m);
+    for (int q = 0; q < n; ++q) {
+      th[q] = std::log(tt[q]);
+      th[n + q] = std::log(ww[q]);
+    }
+    th[2 * n] = E;
+    auto resid = [&](const std::vector<double> &x, std::vector<double> &F) {
+      std::vector<double> t2(n), w2(n);
+      for (int q = 0; q < n; ++q) {
+        t2[q] = std::exp(x[q]);
+        w2[q] = std::exp(x[n + q]);
+      }
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) {
+        F[i] = rel_err(t2, w2, pts[i]) - sg[i] * x[2 * n];
+        s += F[i] * F[i];
+      }
+      return s;
+    };
+    std::vector<double> F(m);
+    double f0 = resid(th, F);
+    for (int nt = 0; nt < 30 && f0 > 0; ++nt) {
+      std::vector<double> Jm((size_t)m * m), rhs(m);
+      for (int i = 0; i < m; ++i) {
+        const double x = pts[i];
+        for (int q = 0; q < n; ++q) {
+          const double tq = std::exp(th[q]), wq = std::exp(th[n + q]), ex = std::exp(-tq * x);
+          Jm[(size_t)i * m + q] = x * x * wq * tq * ex;  // d e / d log t
+          Jm[(size_t)i * m + n + q] = -x * wq * ex;      // d e / d log w
+        }
+        Jm[(size_t)i * m + 2 * n] = -sg[i];
+        rhs[i] = -F[i];
+      }
+      if (!solve_dense(m, Jm, rhs)) break;
+      double lam = 1.0, f1 = 0.0;
+      std::vector<double> th2(m), F2(m);
+      for (int ls = 0; ls < 30; ++ls, lam *= 0.5) {
+        for (int k = 0; k < m; ++k) th2[k] = th[k] + lam * rhs[k];
+        f1 = resid(th2, F2);
+        if (std::isfinite(f1) && f1 < f0) break;
+      }
+      if (!(std::isfinite(f1) && f1 < f0)) break;
+      th = th2;
+      F = F2;
+      f0 = f1;
+    }
+    for (int q = 0; q < n; ++q) {
+      tt[q] = std::exp(th[q]);
+      ww[q] = std::exp(th[n + q]);
+    }
+  }
+  if (!ok) return false;
+  for (double v : tt)
+    if (!(v > 0) || !std::isfinite(v)) return false;
+  std::vector<int> ord(n);
+  for (int q = 0; q < n; ++q) ord[q] = q;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return tt[a] < tt[b]; });
+  for (int q = 0; q < n; ++q) {
+    t[q] = tt[ord[q]];
+    w[q] = ww[ord[q]];
+  }
+  return true;
+}
+
+}  // namespace
+
+int laplace_minimax(double xmin, double xmax, int n, double *t_out, double *w_out,
+                    double *err_out, int *converged) {
+  int rc = laplace_quadrature(xmin, xmax, n, t_out, w_out, nullptr);
+  if (rc) return rc;
+  const double R = xmax / xmin;
+  std::vector<double> t(n), w(n);
+  for (int q = 0; q < n; ++q) {
+    t[q] = t_out[q] * xmin;
+    w[q] = w_out[q] * xmin;
+  }
+  const bool ok = remez(R, n, t, w);
+  if (converged) *converged = ok ? 1 : 0;
+  std::vector<double> tt(n), wt(n);
+  for (int q = 0; q < n; ++q) {
+    tt[q] = t[q] / xmin;
+    wt[q] = w[q] / xmin;
+    t_out[q] = tt[q];
+    w_out[q] = wt[q];
+  }
+  if (err_out) *err_out = max_rel_error(tt, wt, xmin, xmax, 100000);
+  return LTJK_OK;
+}
+
 }  // namespace ltjk

@@ -11,5 +11,7 @@ void normalise_shell(int l, int np, const double *exps, const double *coefs, dou
 void boys_table(int rows, int cols, double step, double *tab);
 int laplace_quadrature(double xmin, double xmax, int n, double *t_out, double *w_out,
                        double *err_out);
+int laplace_minimax(double xmin, double xmax, int n, double *t_out, double *w_out,
+                    double *err_out, int *converged);
 
 }  // namespace ltjk

@@ -65,6 +65,8 @@ SIGNATURES = {
     "ltjk_context_stats": ([_P, _P], _I),
     "ltjk_schwarz": ([_P, _P], _I),
     "ltjk_laplace_quadrature": ([_D, _D, _I, _P, _P, _P], _I),
+    "ltjk_laplace_minimax": ([_D, _D, _I, _P, _P, _P, _P], _I),
+    "ltjk_laplace_shift": ([_I, _P, _P, _D, _P], _I),
     "ltjk_pseudo_densities": ([_P, _I, _I, _P, _P, _P, _P, _I, _P, _I, _P, _P, _P], _I),
     "ltjk_jk_build": ([_P, _I, _P, _P, _P, _P], _I),
     "ltjk_jk_build_noalloc": ([_P, _I, _P, _P, _P, _P], _I),
@@ -134,6 +136,27 @@ def laplace_quadrature(xmin: float, xmax: float, n: int):
                                          t.ctypes.data_as(_P), w.ctypes.data_as(_P),
                                          ctypes.byref(err)))
     return t, w, err.value
+
+
+def laplace_minimax(xmin: float, xmax: float, n: int):
+    """(t, w, max_rel_err, converged) of the minimax exponential sum for 1/x (Eq. laplace)."""
+    t = np.zeros(n)
+    w = np.zeros(n)
+    err = ctypes.c_double(0.0)
+    conv = ctypes.c_int(0)
+    _check(lib().ltjk_laplace_minimax(float(xmin), float(xmax), int(n), t.ctypes.data_as(_P),
+                                      w.ctypes.data_as(_P), ctypes.byref(err), ctypes.byref(conv)))
+    return t, w, err.value, bool(conv.value)
+
+
+def laplace_shift(t, w, omega: float):
+    """Shifted weights w exp(omega t) for 1/(D - omega) (Eq. eomshift)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros_like(w)
+    _check(lib().ltjk_laplace_shift(len(t), t.ctypes.data_as(_P), w.ctypes.data_as(_P),
+                                    float(omega), out.ctypes.data_as(_P)))
+    return out
 
 
 class Context:

@@ -69,3 +69,21 @@ def test_library_laplace_quadrature(L, oracle):
     t1, w1, _ = L.laplace_quadrature(xmin, xmax, 8)
     t2, w2, _ = L.laplace_quadrature(xmin, xmax, 8)
     assert np.array_equal(t1, t2) and np.array_equal(w1, w2)
+
+
+def test_library_minimax_and_shift(L, oracle):
+    """Where the library's Remez exchange converges, it finds the oracle's minimax
+    grid (the best approximation is unique); the shift matches Eq. eomshift."""
+    for (xmin, xmax), n in [((1.2672, 8.502), 4), ((0.2, 20.0), 4), ((0.2, 20.0), 8)]:
+        t, w, err, conv = L.laplace_minimax(xmin, xmax, n)
+        assert conv, (xmin, xmax, n)
+        to, wo, eo = oracle.laplace_minimax(xmin, xmax, n)
+        assert abs(err - eo) <= 1e-3 * eo
+        assert np.allclose(t, to, rtol=1e-4) and np.allclose(w, wo, rtol=1e-4)
+    t, w, err, conv = L.laplace_minimax(1.2672, 8.502, 12)
+    _, _, els = L.laplace_quadrature(1.2672, 8.502, 12)
+    assert err <= els * (1 + 1e-12)  # never worse than the least-squares grid
+    ws = L.laplace_shift(t, w, 0.75)
+    assert np.allclose(ws, oracle.laplace_shift(t, w, 0.75), rtol=1e-14, atol=0)
+    with pytest.raises(L.LtjkError):
+        L.laplace_shift(t, w, float("nan"))

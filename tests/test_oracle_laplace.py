@@ -60,3 +60,32 @@ def test_zero_point_density(oracle):
     w = W.config1()
     D = oracle.pseudo_densities(w.C_occ, w.C_vir, w.eps_occ, w.eps_vir, w.X, np.array([0.0]))
     assert np.allclose(D[0], w.C_occ @ w.X[0] @ w.C_vir.T, rtol=1e-14, atol=1e-12)
+
+
+@pytest.mark.parametrize("rng_,n", [((1.2672, 8.502), 4), ((0.2, 20.0), 4), ((0.2, 20.0), 8)])
+def test_minimax_equioscillates(oracle, rng_, n):
+    """The Remez result is the minimax grid: its relative error alternates in
+    sign at 2n+1 points with equal magnitude (Chebyshev alternation), and its
+    maximum error is below the least-squares grid's."""
+    xmin, xmax = rng_
+    tl, wl, el = oracle.laplace_quadrature(xmin, xmax, n)
+    tm, wm, em = oracle.laplace_minimax(xmin, xmax, n)
+    pts, _ = oracle._alternation_points(tm * xmin, wm * xmin, xmax / xmin, n)
+    ee = oracle._rel_err_fn(tm * xmin, wm * xmin, pts)
+    assert len(pts) == 2 * n + 1
+    assert np.all(np.sign(ee[1:]) != np.sign(ee[:-1]))
+    assert np.abs(ee).max() / np.abs(ee).min() < 1.001
+    assert em < el
+    assert abs(np.abs(ee).max() - em) <= 1e-3 * em
+
+
+def test_eom_shift_identity(oracle):
+    """sum w e^{omega t} e^{-t D} = sum w e^{-t (D - omega)} (Eq. eomshift): the shifted grid
+    has the unshifted grid's error for D - omega in the fitted range."""
+    xmin, xmax = 1.2672, 8.502
+    t, w, err = oracle.laplace_minimax(xmin, xmax, 6)
+    omega = 0.9
+    ws = oracle.laplace_shift(t, w, omega)
+    D = np.geomspace(xmin + omega, xmax + omega, 5001)
+    approx = np.exp(-np.outer(D, t)) @ ws
+    assert np.max(np.abs((D - omega) * approx - 1.0)) <= err * (1 + 1e-9)
