@@ -233,6 +233,18 @@ int ltjk_jk_build_noalloc(ltjk_ctx *ctx, int ndens, const double *D, double *J, 
 int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, double cJ,
                  double cK, double *grad, ltjk_stream stream);
 
+/* ----------------------------------------------- Laplace-Fock back-transform */
+/* F[q] = C_left^T (cJ J[q] + cK K[q]) C_right (Eq. laplacefock with cJ = 2,
+   cK = -1 and C_left = C_right = C): returns each grid point's J/K build to the
+   MO basis; with C_left = C_occ and C_right = C_vir it gives the
+   occupied-virtual block that feeds the next level of the density cascade
+   (Eq. aodensk, through ltjk_pseudo_densities with X = that block).
+     J, K [ndens][N][N], C_left [N][nl], C_right [N][nr] (device, row-major),
+     F [ndens][nl][nr] (device, overwritten).  Uses the context's scratch. */
+int ltjk_laplace_fock(ltjk_ctx *ctx, int ndens, const double *J, const double *K, double cJ,
+                      double cK, int nl, const double *C_left, int nr, const double *C_right,
+                      double *F, ltjk_stream stream);
+
 /* ------------------------------------------------------------- inspection */
 /* Contracted Cartesian integral blocks of nq shell quartets (a,b|c,d) given in
    shells_host[4*nq]; out [sum of block sizes] device FP64, blocks concatenated

@@ -375,3 +375,8 @@ def laplace_shift(t, w, omega):
     """EOM-shifted weights w_q e^{omega t_q} (Eq. eomshift): sum_q w~_q e^{-t_q D}
     approximates 1/(D - omega) wherever D - omega lies in the fitted range."""
     return np.asarray(w) * np.exp(omega * np.asarray(t))
+
+
+def laplace_fock(J, K, C_left, C_right, cJ=2.0, cK=-1.0):
+    """Eq. laplacefock: F[q] = C_left^T (cJ J[q] + cK K[q]) C_right."""
+    return np.einsum("mp,qmn,nr->qpr", C_left, cJ * J + cK * K, C_right, optimize=True)

@@ -858,6 +858,33 @@ int ltjk_pseudo_densities(ltjk_ctx *ctx, int nocc, int nvir, const double *C_occ
   return LTJK_OK;
 }
 
+int ltjk_laplace_fock(ltjk_ctx *ctx, int ndens, const double *J, const double *K, double cJ,
+                      double cK, int nl, const double *C_left, int nr, const double *C_right,
+                      double *F, ltjk_stream stream) {
+  if (!ctx || !J || !K || !C_left || !C_right || !F)
+    return set_error(LTJK_EINVAL, "laplace_fock: null argument");
+  if (ndens < 1 || ndens > 4096 || nl < 1 || nr < 1)
+    return set_error(LTJK_EINVAL, "laplace_fock: bad sizes");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int N = ctx->nao;
+  const size_t nm = (size_t)ndens * N * N, nt = (size_t)ndens * N * nr;
+  int rc = ctx->ensure_scratch((nm + nt) * sizeof(double), st);
+  if (rc) return rc;
+  double *M = ctx->scratch.as<double>(), *T = M + nm;
+  combine_jk<<<(int)std::min<size_t>((nm + 255) / 256, 152 * 16), 256, 0, st>>>(J, K, cJ, cK, M, nm);
+  dim3 thr(16, 16);
+  // T[q] = M[q] C_right            ([N][N] x [N][nr])
+  gemm_f64<false><<<dim3((nr + 15) / 16, (N + 15) / 16, ndens), thr, 0, st>>>(
+      M, (long long)N * N, C_right, 0, T, (long long)N * nr, N, nr, N, N, nr, nr);
+  // F[q] = C_left^T T[q]           ([nl][N] x [N][nr])
+  gemm_f64<false, true><<<dim3((nr + 15) / 16, (nl + 15) / 16, ndens), thr, 0, st>>>(
+      C_left, 0, T, (long long)N * nr, F, (long long)nl * nr, nl, nr, N, nl, nr, nr);
+  CUDA_TRY(cudaGetLastError());
+  g_launches += 3;
+  return LTJK_OK;
+}
+
 int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int precision, double *out,
                         ltjk_stream stream) {
   if (!ctx || !shells_host || !out || nq < 0) return set_error(LTJK_EINVAL, "shell_quartets: bad argument");

@@ -627,9 +627,10 @@ __global__ void scale_amplitudes(const double *__restrict__ X, const double *__r
   }
 }
 
-// Batched FP64 GEMM with 16x16 tiles, C[b][m][n] = sum_k A(b)[m][k] Bop(b)[k][n],
-// Bop[k][n] = B[n][k] when TRANSB else B[k][n].  Row-major, leading dims lda/ldb/ldc.
-template <bool TRANSB>
+// Batched FP64 GEMM with 16x16 tiles, C[b][m][n] = sum_k Aop(b)[m][k] Bop(b)[k][n],
+// Aop[m][k] = A[k][m] when TRANSA else A[m][k]; Bop[k][n] = B[n][k] when TRANSB
+// else B[k][n].  Row-major, leading dims lda/ldb/ldc.
+template <bool TRANSB, bool TRANSA = false>
 __global__ void gemm_f64(const double *__restrict__ A, long long strideA,
                          const double *__restrict__ Bm, long long strideB, double *__restrict__ C,
                          long long strideC, int M, int Nn, int Kd, int lda, int ldb, int ldc) {
@@ -641,7 +642,10 @@ __global__ void gemm_f64(const double *__restrict__ A, long long strideA,
   const int m0 = blockIdx.y * 16, n0 = blockIdx.x * 16;
   double acc = 0.0;
   for (int k0 = 0; k0 < Kd; k0 += 16) {
-    As[ty][tx] = (m0 + ty < M && k0 + tx < Kd) ? Ab[(size_t)(m0 + ty) * lda + k0 + tx] : 0.0;
+    if (TRANSA)  // thread (tx,ty) reads A[k0+ty][m0+tx] (coalesced in tx) -> As[m=tx][k=ty]
+      As[tx][ty] = (k0 + ty < Kd && m0 + tx < M) ? Ab[(size_t)(k0 + ty) * lda + m0 + tx] : 0.0;
+    else
+      As[ty][tx] = (m0 + ty < M && k0 + tx < Kd) ? Ab[(size_t)(m0 + ty) * lda + k0 + tx] : 0.0;
     if (TRANSB)  // thread (tx,ty) reads B[n0+ty][k0+tx] (coalesced in tx) -> Bs[k=tx][n=ty]
       Bs[tx][ty] = (n0 + ty < Nn && k0 + tx < Kd) ? Bb[(size_t)(n0 + ty) * ldb + k0 + tx] : 0.0;
     else         // thread (tx,ty) reads B[k0+ty][n0+tx] -> Bs[k=ty][n=tx]
@@ -652,6 +656,13 @@ __global__ void gemm_f64(const double *__restrict__ A, long long strideA,
     __syncthreads();
   }
   if (m0 + ty < M && n0 + tx < Nn) Cb[(size_t)(m0 + ty) * ldc + n0 + tx] = acc;
+}
+
+// M = cJ J + cK K, elementwise.
+__global__ void combine_jk(const double *__restrict__ J, const double *__restrict__ K, double cJ,
+                           double cK, double *__restrict__ M, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    M[t] = cJ * J[t] + cK * K[t];
 }
 
 }  // namespace ltjk

@@ -72,6 +72,7 @@ SIGNATURES = {
     "ltjk_jk_build_noalloc": ([_P, _I, _P, _P, _P, _P], _I),
     "ltjk_jk_grad": ([_P, _I, _P, _P, _D, _D, _P, _P], _I),
     "ltjk_shell_quartets": ([_P, _I, _P, _I, _P, _P], _I),
+    "ltjk_laplace_fock": ([_P, _I, _P, _P, _D, _D, _I, _P, _I, _P, _P, _P], _I),
     "ltjk_service_create": ([ctypes.c_size_t, _I, _P], _I),
     "ltjk_service_submit": ([_P, _P, _P], _I),
     "ltjk_service_poll": ([_P, ctypes.c_uint64, _P], _I),
@@ -251,6 +252,18 @@ class Context:
             _dev(X, (npair, no, nv), "X"), nlap, t.ctypes.data_as(_P),
             _dev(D, (nlap * npair, N, N), "D"), _stream(stream)))
         return D
+
+    def laplace_fock(self, J, K, C_left, C_right, cJ=2.0, cK=-1.0, F=None, stream=None):
+        """F[q] = C_left^T (cJ J[q] + cK K[q]) C_right (Eq. laplacefock)."""
+        nd, N = J.shape[0], self.nao
+        nl, nr = C_left.shape[1], C_right.shape[1]
+        if F is None:
+            F = torch.empty((nd, nl, nr), dtype=torch.float64, device=J.device)
+        _check(lib().ltjk_laplace_fock(self._h, nd, _dev(J, (nd, N, N), "J"), _dev(K, (nd, N, N), "K"),
+                                       float(cJ), float(cK), nl, _dev(C_left, (N, nl), "C_left"), nr,
+                                       _dev(C_right, (N, nr), "C_right"), _dev(F, (nd, nl, nr), "F"),
+                                       _stream(stream)))
+        return F
 
     def shell_quartets(self, quartets, precision=FP64, stream=None):
         """Contracted blocks of (a b|c d) for each (a,b,c,d) in canonical pair order."""
