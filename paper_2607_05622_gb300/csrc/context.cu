@@ -34,6 +34,10 @@ constexpr long long kTargetItems = 152 * 24;  // work items a class should offer
 constexpr int kSideStreams = 4;          // class launches of one build run on these concurrently
 constexpr int kSmemBudget = 200 * 1024;  // bytes of shared memory per CTA we plan for
 constexpr int kMaxSmem = 227 * 1024;
+constexpr int kSmemPerSM = 228 * 1024;      // shared memory of one SM
+constexpr int kSmemPerCTAReserved = 1024;   // the driver's share of each CTA
+constexpr int kRegsPerSM = 65536;
+constexpr int kMaxCTAsPerSM = 32;
 constexpr double kPrimPairDrop = 1e-18;  // drop primitive pair iff K_AB |c_a c_b| below this
 
 // Device buffer owned by a context.  Stream-ordered allocation
@@ -170,19 +174,42 @@ ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
   return cl;
 }
 
+// Warps per CTA that put the most warps on an SM, given the shared memory one
+// warp needs and the kernel's registers per thread: a heavy class whose warp
+// needs 30 KB fits seven one-warp CTAs on an SM but only one four-warp CTA.
+int warps_per_cta(int smem_per_warp, int regs) {
+  const int regs_per_warp = ((regs + 7) / 8 * 8) * 32;
+  int best_w = 1, best = 0;
+  for (int w : {4, 2, 1}) {
+    if (w > 1 && w * smem_per_warp > kSmemBudget) continue;
+    const int by_smem = kSmemPerSM / (w * smem_per_warp + kSmemPerCTAReserved);
+    const int by_regs = kRegsPerSM / (regs_per_warp * w);
+    const int ctas = std::min({by_smem, by_regs, kMaxCTAsPerSM});
+    if (ctas * w > best) {
+      best = ctas * w;
+      best_w = w;
+    }
+  }
+  return best_w;
+}
+
 template <typename Real, int MODE>
-int launch_class(const DevProgs &PR, const ClassLaunch &cl, const JobTable &T, cudaStream_t st) {
+int launch_class(const DevProgs &PR, const ClassLaunch &cl_in, const JobTable &T, cudaStream_t st) {
   if (T.total <= 0) return LTJK_OK;
+  static std::atomic<int> regs{0};  // per instantiation
+  if (regs.load() == 0) {
+    CUDA_TRY(cudaFuncSetAttribute(quartet_kernel<Real, MODE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    cudaFuncAttributes fa{};
+    CUDA_TRY(cudaFuncGetAttributes(&fa, quartet_kernel<Real, MODE>));
+    regs.store(fa.numRegs > 0 ? fa.numRegs : 128);
+  }
+  ClassLaunch cl = cl_in;
+  cl.warps = warps_per_cta(cl.smem_per_warp, regs.load());
   const size_t smem = (size_t)cl.smem_per_warp * cl.warps;
   if (smem > (size_t)kMaxSmem)
     return set_error(LTJK_EUNSUPPORTED, "class (%d%d|%d%d) needs %zu bytes of shared memory",
                      cl.p.la, cl.p.lb, cl.p.lc, cl.p.ld, smem);
-  static bool attr_set = false;  // per instantiation
-  if (!attr_set) {
-    CUDA_TRY(cudaFuncSetAttribute(quartet_kernel<Real, MODE>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
-    attr_set = true;
-  }
   const int ctas_needed = (T.total + cl.warps - 1) / cl.warps;
   const int grid = std::min(ctas_needed, 152 * 32);
   quartet_kernel<Real, MODE><<<grid, 32 * cl.warps, smem, st>>>(PR, cl, T);

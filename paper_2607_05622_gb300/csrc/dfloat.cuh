@@ -59,15 +59,42 @@ __device__ __forceinline__ float d2f_bits(double x) {
   return __fadd_rn(h, l);
 }
 
+// hi + lo rounded to double with integer operations only (no FP64 add, which
+// on this part costs as much as ~60 FP32 instructions).  hi converts exactly;
+// lo is added as an integer number of units in the last place of that double
+// (half-units rounded away from zero).  Requires |lo| < ulp(hi), which holds for
+// every normalised double-float and for the split of a double; then the sum
+// never carries out of the mantissa field, and the one borrow (hi a power of
+// two, lo of opposite sign) is handled by counting in the half-size units of
+// the binade below.
+__device__ __forceinline__ double df_to_double(float hi, float lo) {
+  const unsigned uh = __float_as_uint(hi), ul = __float_as_uint(lo);
+  const int eh = (int)((uh >> 23) & 0xFFu), el = (int)((ul >> 23) & 0xFFu);
+  if (eh == 0 || eh == 0xFF) return f2d_bits(hi);
+  unsigned long long H = ((unsigned long long)(uh & 0x80000000u) << 32) |
+                         ((unsigned long long)(eh + 896) << 52) |
+                         ((unsigned long long)(uh & 0x7FFFFFu) << 29);
+  if (el == 0) return __longlong_as_double((long long)H);
+  const bool opp = ((uh ^ ul) & 0x80000000u) != 0u;
+  int s = el - eh + 29;  // |lo| / ulp(H) = mantissa(lo) * 2^s
+  if (opp && (uh & 0x7FFFFFu) == 0u) s += 1;
+  const unsigned long long ml = (unsigned long long)((ul & 0x7FFFFFu) | 0x800000u);
+  unsigned long long off = 0ull;
+  if (s >= 0)
+    off = ml << s;
+  else if (s > -40)
+    off = (ml + (1ull << (-s - 1))) >> (-s);
+  H = opp ? H - off : H + off;
+  return __longlong_as_double((long long)H);
+}
+
 struct dflt {
   float hi, lo;
   __device__ __forceinline__ dflt() {}
   __device__ __forceinline__ dflt(float h, float l) : hi(h), lo(l) {}
   __device__ __forceinline__ explicit dflt(double x) { d2f_split(x, hi, lo); }
   __device__ __forceinline__ explicit dflt(int n) : hi((float)n), lo(0.0f) {}
-  __device__ __forceinline__ explicit operator double() const {
-    return f2d_bits(hi) + f2d_bits(lo);
-  }
+  __device__ __forceinline__ explicit operator double() const { return df_to_double(hi, lo); }
 };
 
 // a + b, double-word (two-sum of the leading words, then renormalise)

@@ -421,53 +421,71 @@ __device__ __forceinline__ const dflt *digest_operand<dflt>(const JKArgs &a, boo
   return isJ ? a.S2 : a.D2;
 }
 
+// One placement of the digestion, out(x, y) += sum_{u<nu, v<nv} I[x sr + y sc +
+// u su + v sv] M(u, v), for every output (x, y) of the nout = nr x nc block and
+// every density.  Lanes run over (output group, density) units, four outputs per
+// group sharing each density load (four independent accumulation chains), so a
+// warp stays full when the number of densities is not a multiple of 32.  The
+// sums stay runtime loops: unrolled per block shape, the double-float code of
+// the ten placements outgrows the instruction cache and stalls every warp on
+// the SM, the recurrence's included.
+template <typename Real>
+__device__ __forceinline__ void digest_place(const Real *__restrict__ I, const Real *__restrict__ Mblk,
+                                             double *__restrict__ Tblk, int nd, size_t mrow, int nout,
+                                             int nc, int sr, int sc, int su, int sv, int nu, int nv,
+                                             int lane) {
+  const int ngrp = (nout + 3) >> 2;
+  const unsigned inv_nc = (65536u + (unsigned)nc - 1u) / (unsigned)nc;  // o / nc exact for o < 2^10
+  int q = lane, grp = 0;
+  while (q >= nd) { q -= nd; ++grp; }
+  while (grp < ngrp) {
+    const int o0 = grp << 2, cnt = min(4, nout - o0);
+    const Real *Ib[4];
+    size_t to[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = o0 + (j < cnt ? j : 0);
+      const int x = (int)(((unsigned)o * inv_nc) >> 16), y = o - x * nc;
+      Ib[j] = I + x * sr + y * sc;
+      to[j] = (size_t)x * mrow + (size_t)y * nd + q;
+    }
+    Real acc0 = zero_real<Real>(), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+    const Real *Mu = Mblk + q;
+    for (int u = 0; u < nu; ++u, Mu += mrow) {
+      const int iu = u * su;
+      for (int v = 0; v < nv; ++v) {
+        const Real m = ldg(Mu + (size_t)v * nd);
+        const int iv = iu + v * sv;
+        acc0 = fma(Ib[0][iv], m, acc0);
+        acc1 = fma(Ib[1][iv], m, acc1);
+        acc2 = fma(Ib[2][iv], m, acc2);
+        acc3 = fma(Ib[3][iv], m, acc3);
+      }
+    }
+    atomicAdd(Tblk + to[0], to_double(acc0));
+    if (cnt > 1) atomicAdd(Tblk + to[1], to_double(acc1));
+    if (cnt > 2) atomicAdd(Tblk + to[2], to_double(acc2));
+    if (cnt > 3) atomicAdd(Tblk + to[3], to_double(acc3));
+    q += 32;
+    while (q >= nd) { q -= nd; ++grp; }
+  }
+}
+
 template <typename Real>
 __device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], const int n[4], int N,
                           int lane) {
   const int str[4] = {n[1] * n[2] * n[3], n[2] * n[3], n[3], 1};
   const int nd = a.nd;
+  const size_t mrow = (size_t)N * nd;  // stride of one AO row in the q-innermost layout
   for (int pl = 0; pl < 10; ++pl) {
     const Placement P = c_place[pl];
     if (P.isJ ? a.J == nullptr : a.K == nullptr) continue;
     const Real *M = digest_operand<Real>(a, P.isJ);
     double *T = P.isJ ? a.J : a.K;
-    const int nr = n[P.orow], nc = n[P.ocol], nu = n[P.srow], nv = n[P.scol];
-    const int sr = str[P.orow], sc = str[P.ocol], su = str[P.srow], sv = str[P.scol];
     const Real *Mblk = M + ((size_t)off[P.srow] * N + off[P.scol]) * nd;
-    const size_t mrow = (size_t)N * nd;  // stride of one AO row in the q-innermost layout
-    // output coordinates are warp-uniform; lanes run over densities; four
-    // outputs per pass share each density load and give four independent
-    // accumulation chains
-    const int nout = nr * nc;
-    for (int o0 = 0; o0 < nout; o0 += 4) {
-      const Real *Ib[4];
-      double *To[4];
-      const int cnt = min(4, nout - o0);
-      for (int j = 0; j < 4; ++j) {
-        const int o = o0 + (j < cnt ? j : 0), x = o / nc, y = o - (o / nc) * nc;
-        Ib[j] = I + x * sr + y * sc;
-        To[j] = T + ((size_t)(off[P.orow] + x) * N + off[P.ocol] + y) * nd;
-      }
-      for (int q = lane; q < nd; q += 32) {
-        Real acc0 = zero_real<Real>(), acc1 = acc0, acc2 = acc0, acc3 = acc0;
-        const Real *Mu = Mblk + q;
-        for (int u = 0; u < nu; ++u, Mu += mrow) {
-          const int iu = u * su;
-          for (int v = 0; v < nv; ++v) {
-            const Real m = ldg(Mu + (size_t)v * nd);
-            const int iv = iu + v * sv;
-            acc0 = fma(Ib[0][iv], m, acc0);
-            acc1 = fma(Ib[1][iv], m, acc1);
-            acc2 = fma(Ib[2][iv], m, acc2);
-            acc3 = fma(Ib[3][iv], m, acc3);
-          }
-        }
-        atomicAdd(To[0] + q, to_double(acc0));
-        if (cnt > 1) atomicAdd(To[1] + q, to_double(acc1));
-        if (cnt > 2) atomicAdd(To[2] + q, to_double(acc2));
-        if (cnt > 3) atomicAdd(To[3] + q, to_double(acc3));
-      }
-    }
+    double *Tblk = T + ((size_t)off[P.orow] * N + off[P.ocol]) * nd;
+    digest_place<Real>(I, Mblk, Tblk, nd, mrow, n[P.orow] * n[P.ocol], n[P.ocol], str[P.orow],
+                       str[P.ocol], str[P.srow], str[P.scol], n[P.srow], n[P.scol], lane);
   }
 }
 
@@ -503,8 +521,11 @@ __device__ void gamma_block(const JKArgs &a, double *gam, const int off[4], cons
 
 // ------------------------------------------------------------- the kernel
 // One warp per work item (bra pair, ket range); warps of a CTA are independent.
+// 128 registers per thread: the J/K kernels also fit 80 or 96 without spills,
+// but the extra warps do not make up for the lost scheduling freedom (measured
+// 8 % slower on the 200-AO chain), and the gradient kernels spill below 128.
 template <typename Real, int MODE>
-__global__ void __launch_bounds__(128) quartet_kernel(DevProgs PR, ClassLaunch CL,
+__global__ void __launch_bounds__(128, 4) quartet_kernel(DevProgs PR, ClassLaunch CL,
                                                       const __grid_constant__ JobTable T) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

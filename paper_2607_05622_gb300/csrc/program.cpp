@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <array>
 #include <map>
+#include <set>
 #include <stdexcept>
 #include <tuple>
 
@@ -184,6 +185,50 @@ struct HrrGen {
   }
 };
 
+// Liveness-based slot assignment for a level-ordered program.  Entry k runs
+// at level lev[k] (nondecreasing over the writers), writes node tgt[k] (or
+// nothing when tgt[k] < 0) and reads the nodes in src[k]; nodes below `fixed`
+// keep their numbers.  A node's slot returns to the free pool once every level
+// that reads it has finished (the kernel synchronises the warp between levels,
+// so a step of level L may take any slot whose last reader ran at a level < L);
+// nodes marked in `pinned` are never released.  Returns the new number of every
+// node and, in *size, the number of slots used (fixed ones included).
+std::vector<int> assign_slots(int nnodes, int fixed, const std::vector<int> &lev,
+                              const std::vector<int> &tgt, const std::vector<std::vector<int>> &src,
+                              const std::vector<char> &pinned, int *size) {
+  std::vector<int> last(nnodes, -1);
+  for (size_t k = 0; k < tgt.size(); ++k)
+    for (int x : src[k])
+      if (x >= fixed) last[x] = std::max(last[x], lev[k]);
+  std::vector<int> map(nnodes, -1);
+  for (int x = 0; x < fixed; ++x) map[x] = x;
+  std::set<int> pool;
+  std::multimap<int, int> release;  // last-use level -> slot
+  int next = fixed, cur = -1;
+  for (size_t k = 0; k < tgt.size(); ++k) {
+    if (tgt[k] < 0) continue;
+    if (lev[k] < cur) throw std::runtime_error("assign_slots: writers out of level order");
+    if (lev[k] != cur) {
+      cur = lev[k];
+      while (!release.empty() && release.begin()->first < cur) {
+        pool.insert(release.begin()->second);
+        release.erase(release.begin());
+      }
+    }
+    int sl;
+    if (!pool.empty()) {
+      sl = *pool.begin();
+      pool.erase(pool.begin());
+    } else {
+      sl = next++;
+    }
+    map[tgt[k]] = sl;
+    if (!pinned[tgt[k]]) release.emplace(std::max(last[tgt[k]], lev[k]), sl);
+  }
+  *size = next;
+  return map;
+}
+
 }  // namespace
 
 void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv, ClassProg &P) {
@@ -254,8 +299,33 @@ void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv
     }
     ps.levels.push_back((int)ps.vrr.size());
     P.nvrr_level = (int)ps.levels.size() - 1 - P.vrr_level0;
-    P.vrr_size = (int)vg.level.size();
     P.vrr_flops = vg.flops;
+    // compact the VRR region: slots of intermediates that no later level reads
+    // are reused; the targets the accumulation reads stay to the end
+    const int nnodes = (int)vg.level.size(), fixed = P.ltot + 2;
+    std::vector<int> lev, tgt;
+    std::vector<std::vector<int>> src;
+    for (int k : order) {
+      const VrrInstr &in = vg.instr[k];
+      lev.push_back(vg.instr_level[k]);
+      tgt.push_back(in.tgt);
+      src.push_back({in.s0, in.s1, in.s2, in.s3, in.s4});
+    }
+    std::vector<char> pinned(nnodes, 0);
+    for (const AccInstr &a : accs) pinned[a.slot] = 1;
+    int size = 0;
+    const std::vector<int> map = assign_slots(nnodes, fixed, lev, tgt, src, pinned, &size);
+    for (int k = P.vrr_begin; k < (int)ps.vrr.size(); ++k) {
+      VrrInstr &in = ps.vrr[k];
+      in.tgt = (uint16_t)map[in.tgt];
+      in.s0 = (uint16_t)map[in.s0];
+      in.s1 = (uint16_t)map[in.s1];
+      in.s2 = (uint16_t)map[in.s2];
+      in.s3 = (uint16_t)map[in.s3];
+      in.s4 = (uint16_t)map[in.s4];
+    }
+    for (AccInstr &a : accs) a.slot = (uint16_t)map[a.slot];
+    P.vrr_size = size;
   }
   P.acc_begin = (int)ps.acc.size();
   P.nacc = (int)accs.size();
@@ -318,10 +388,10 @@ void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv
           }
     TileProg T{};
     T.nout = (int)final_instr.size();
-    T.out_base = hg.acc_total + (int)hg.level.size();
-    if (T.out_base + T.nout > 65000) throw std::runtime_error("HRR output block too large");
+    const int nodes_end = hg.acc_total + (int)hg.level.size();  // first output node
+    if (nodes_end + T.nout > 65000) throw std::runtime_error("HRR output block too large");
     for (size_t k = 0; k < final_instr.size(); ++k) {
-      final_instr[k].tgt = (uint16_t)(T.out_base + k);
+      final_instr[k].tgt = (uint16_t)(nodes_end + k);
       hg.instr.push_back(final_instr[k]);
       hg.instr_level.push_back(final_level[k]);
     }
@@ -329,6 +399,28 @@ void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
     std::stable_sort(order.begin(), order.end(),
                      [&](int u, int v) { return hg.instr_level[u] < hg.instr_level[v]; });
+    // Slots: accumulators and the zero slot keep their numbers, the output
+    // block follows them contiguously, and the intermediates share a pool
+    // above it by liveness.
+    T.out_base = hg.acc_total + 1;
+    const int fixed = hg.acc_total + 1;
+    std::vector<int> lev, tgt;
+    std::vector<std::vector<int>> src;
+    for (int k : order) {
+      const HrrInstr &in = hg.instr[k];
+      lev.push_back(hg.instr_level[k]);
+      tgt.push_back(in.tgt < nodes_end ? (int)in.tgt : -1);  // outputs are placed directly
+      src.push_back({in.s0, in.s1});
+    }
+    int pool_size = 0;
+    const std::vector<int> pool_map =
+        assign_slots(nodes_end, fixed, lev, tgt, src, std::vector<char>(nodes_end, 0), &pool_size);
+    const int pool_base = T.out_base + T.nout;
+    auto remap = [&](int x) {
+      if (x < fixed) return x;
+      if (x >= nodes_end) return T.out_base + (x - nodes_end);
+      return pool_base + (pool_map[x] - fixed);
+    };
     T.hrr_level0 = (int)ps.levels.size();
     int cur = -1;
     for (int k : order) {
@@ -336,11 +428,15 @@ void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv
         cur = hg.instr_level[k];
         ps.levels.push_back((int)ps.hrr.size());
       }
-      ps.hrr.push_back(hg.instr[k]);
+      HrrInstr in = hg.instr[k];
+      in.tgt = (uint16_t)remap(in.tgt);
+      in.s0 = (uint16_t)remap(in.s0);
+      in.s1 = (uint16_t)remap(in.s1);
+      ps.hrr.push_back(in);
     }
     ps.levels.push_back((int)ps.hrr.size());
     T.nhrr_level = (int)ps.levels.size() - 1 - T.hrr_level0;
-    T.hrr_size = (int)hg.level.size() + T.nout;  // zero slot + intermediates + outputs
+    T.hrr_size = 1 + T.nout + (pool_size - fixed);  // zero slot, outputs, pool
     P.hrr_size = std::max(P.hrr_size, T.hrr_size);
     P.hrr_flops += hg.flops;
     ps.tiles.push_back(T);
