@@ -254,6 +254,27 @@ int ltjk_laplace_fock(ltjk_ctx *ctx, int ndens, const double *J, const double *K
 int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int precision,
                         double *out, ltjk_stream stream);
 
+/* The recurrence program of one shell-quartet class (the Obara-Saika vertical
+   and Head-Gordon-Pople horizontal recurrences of the paper's "Computational
+   Details", generated once per process): sizes and the flop model.  Generates
+   and validates every program on first use (every slot in range, and no
+   recurrence level writes a slot that the same level reads, so the lanes of a
+   warp can run a level's steps in any order).  Host-only, no device needed.
+     0 <= la, lb, lc, ld <= LTJK_MAX_L; deriv 0 (integrals) or 1 (derivative
+     integrals, one extra unit of angular momentum); *out is overwritten.
+   LTJK_EUNSUPPORTED for l above LTJK_MAX_L, LTJK_EINVAL for a null out. */
+typedef struct {
+  int ltot;              /* la+lb+lc+ld (+1 for derivatives) */
+  int vrr_steps, vrr_levels, vrr_slots;   /* vertical recurrence per primitive quartet */
+  int accumulators;      /* contracted [e0|f0] values, all channels */
+  int hrr_steps, hrr_levels, hrr_slots;   /* horizontal recurrence, largest output tile */
+  int tiles, outputs;    /* output tiles and integrals per tile (na nb nc nd) */
+  double vrr_flops;      /* flop model per primitive quartet (recurrence only) */
+  double hrr_flops;      /* flop model per contracted quartet */
+  size_t smem_per_warp[3]; /* bytes per warp: IEEE FP64, double-float, FP32 */
+} ltjk_program_info;
+int ltjk_class_program(int la, int lb, int lc, int ld, int deriv, ltjk_program_info *out);
+
 /* --------------------------------------------------------------- serving */
 /* A continuous-batching solver service on one device.  A scheduler thread
    admits submitted requests first-come-first-served whenever their device

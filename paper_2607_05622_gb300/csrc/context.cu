@@ -935,6 +935,42 @@ int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int preci
   return store_blocks(*ctx, qs, precision, offs, out, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int ltjk_class_program(int la, int lb, int lc, int ld, int deriv, ltjk_program_info *out) {
+  if (!out) return set_error(LTJK_EINVAL, "class_program: null argument");
+  if (deriv != 0 && deriv != 1) return set_error(LTJK_EINVAL, "class_program: deriv must be 0 or 1");
+  for (int l : {la, lb, lc, ld})
+    if (l < 0 || l > kMaxL)
+      return set_error(LTJK_EUNSUPPORTED, "class_program: l = %d outside 0..%d", l, kMaxL);
+  const ProgramSet *ps;
+  int rc = program_set(&ps);
+  if (rc) return rc;
+  // programs are stored for l_a >= l_b and l_c >= l_d
+  if (la < lb) std::swap(la, lb);
+  if (lc < ld) std::swap(lc, ld);
+  const ClassProg &p = ps->progs[quartet_index(la, lb, lc, ld, deriv)];
+  *out = ltjk_program_info{};
+  out->ltot = p.ltot;
+  out->vrr_levels = p.nvrr_level;
+  out->vrr_steps = p.nvrr_level ? ps->levels[p.vrr_level0 + p.nvrr_level] - ps->levels[p.vrr_level0] : 0;
+  out->vrr_slots = p.vrr_size;
+  out->accumulators = p.acc_total;
+  out->hrr_slots = p.hrr_size;
+  out->tiles = p.ntile;
+  out->outputs = p.nout;
+  for (int t = 0; t < p.ntile; ++t) {
+    const TileProg &T = ps->tiles[p.tile_begin + t];
+    const int steps = ps->levels[T.hrr_level0 + T.nhrr_level] - ps->levels[T.hrr_level0];
+    out->hrr_steps = std::max(out->hrr_steps, steps);
+    out->hrr_levels = std::max(out->hrr_levels, T.nhrr_level);
+  }
+  out->vrr_flops = p.vrr_flops;
+  out->hrr_flops = p.hrr_flops;
+  out->smem_per_warp[0] = make_launch(p, sizeof(double)).smem_per_warp;
+  out->smem_per_warp[1] = make_launch(p, sizeof(dflt)).smem_per_warp;
+  out->smem_per_warp[2] = make_launch(p, sizeof(float)).smem_per_warp;
+  return LTJK_OK;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------- allocation-free J/K build

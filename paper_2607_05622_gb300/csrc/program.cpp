@@ -459,6 +459,35 @@ static void validate(const ProgramSet &ps, const ClassProg &P) {
     if (in.kind > 1 || in.dir > 2) bad("VRR kind/dir");
     if (in.n1 >= 2 * kMaxLDeriv + 2 || in.n2 >= 2 * kMaxLDeriv + 2) bad("VRR multiplier");
   }
+  // the steps of one level run concurrently on the lanes of a warp: none may
+  // write a slot that the level reads, and no two may write the same slot
+  auto level_hazards = [&](const std::vector<int> &reads, const std::vector<int> &writes) {
+    std::set<int> w;
+    for (int x : writes)
+      if (!w.insert(x).second) bad("two steps of one level write the same slot");
+    for (int x : reads)
+      if (w.count(x)) bad("a level writes a slot that it reads");
+  };
+  for (int L = 0; L < P.nvrr_level; ++L) {
+    std::vector<int> rd, wr;
+    for (int k = ps.levels[P.vrr_level0 + L]; k < ps.levels[P.vrr_level0 + L + 1]; ++k) {
+      const VrrInstr &in = ps.vrr[k];
+      rd.insert(rd.end(), {in.s0, in.s1, in.s2, in.s3, in.s4});
+      wr.push_back(in.tgt);
+    }
+    level_hazards(rd, wr);
+  }
+  for (int t = 0; t < P.ntile; ++t) {
+    const TileProg &T = ps.tiles[P.tile_begin + t];
+    for (int L = 0; L < T.nhrr_level; ++L) {
+      std::vector<int> rd, wr;
+      for (int k = ps.levels[T.hrr_level0 + L]; k < ps.levels[T.hrr_level0 + L + 1]; ++k) {
+        rd.insert(rd.end(), {ps.hrr[k].s0, ps.hrr[k].s1});
+        wr.push_back(ps.hrr[k].tgt);
+      }
+      level_hazards(rd, wr);
+    }
+  }
   for (int k = P.acc_begin; k < P.acc_begin + P.nacc; ++k) {
     const AccInstr &a = ps.acc[k];
     if (a.slot >= P.vrr_size || a.acc >= P.acc_total || a.chan >= P.nchan) bad("ACC index");

@@ -51,6 +51,19 @@ class CtxStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ProgramInfo(ctypes.Structure):
+    _fields_ = [("ltot", ctypes.c_int), ("vrr_steps", ctypes.c_int), ("vrr_levels", ctypes.c_int),
+                ("vrr_slots", ctypes.c_int), ("accumulators", ctypes.c_int), ("hrr_steps", ctypes.c_int),
+                ("hrr_levels", ctypes.c_int), ("hrr_slots", ctypes.c_int), ("tiles", ctypes.c_int),
+                ("outputs", ctypes.c_int), ("vrr_flops", ctypes.c_double), ("hrr_flops", ctypes.c_double),
+                ("smem_per_warp", ctypes.c_size_t * 3)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["smem_per_warp"] = list(self.smem_per_warp)
+        return d
+
+
 _lib = None
 
 # exported symbols and their signatures (restype int unless noted)
@@ -72,6 +85,7 @@ SIGNATURES = {
     "ltjk_jk_build_noalloc": ([_P, _I, _P, _P, _P, _P], _I),
     "ltjk_jk_grad": ([_P, _I, _P, _P, _D, _D, _P, _P], _I),
     "ltjk_shell_quartets": ([_P, _I, _P, _I, _P, _P], _I),
+    "ltjk_class_program": ([_I, _I, _I, _I, _I, _P], _I),
     "ltjk_laplace_fock": ([_P, _I, _P, _P, _D, _D, _I, _P, _I, _P, _P, _P], _I),
     "ltjk_service_create": ([ctypes.c_size_t, _I, _P], _I),
     "ltjk_service_submit": ([_P, _P, _P], _I),
@@ -126,6 +140,14 @@ def launch_count() -> int:
     c = ctypes.c_ulonglong(0)
     _check(lib().ltjk_launch_count(ctypes.byref(c)))
     return c.value
+
+
+def class_program(la: int, lb: int, lc: int, ld: int, deriv: int = 0) -> dict:
+    """ltjk_class_program: sizes and flop model of one class's recurrence program
+    (host-only; generates and validates every program on first use)."""
+    info = ProgramInfo()
+    _check(lib().ltjk_class_program(la, lb, lc, ld, deriv, ctypes.byref(info)))
+    return info.as_dict()
 
 
 def laplace_quadrature(xmin: float, xmax: float, n: int):
