@@ -29,6 +29,12 @@ from paper_2607_05622_gb300 import workloads as W  # noqa: E402
 
 HBM_L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the class launches
+# of one J/K build of this workload, summed from one ncu capture of the current
+# quartet kernel (each launch replayed with flushed caches); None where not
+# captured.  Must be re-taken (or set to None) whenever the kernel changes.
+NCU_DRAM_BYTES_PER_BUILD = {"fp64": None, "mixed": 608.0e6, "fp64-native": None}
+
 
 def measured_peaks():
     try:
@@ -181,6 +187,78 @@ def run_reference(args, world, rank):
 
 
 # ------------------------------------------------------------------ GPU path
+def _event_ms(torch, stream, fn, reps):
+    """Mean device time of fn() over reps calls, CUDA events on `stream`."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_gradient(ltjk, torch, dev, local, stream, prec, reps=3):
+    """ERI-derivative contraction (Eq. jkderiv) on the 200-AO chain geometry with
+    16 separable symmetric terms: gradients/s, quartets/s, and the error against
+    an IEEE FP64 gradient on the same GPU."""
+    wl = W.config4()
+    ctx = ltjk.Context(wl.mol, schwarz_tau=wl.schwarz_tau, mixed_tau=1e-6, precision=prec, device=local)
+    P = torch.from_numpy(wl.P).to(dev)
+    Q = torch.from_numpy(wl.Q).to(dev)
+    g = torch.empty((wl.mol.natoms, 3), dtype=torch.float64, device=dev)
+    ctx.jk_grad(P, Q, wl.cJ, wl.cK, grad=g)
+    ms = _event_ms(torch, stream, lambda: ctx.jk_grad(P, Q, wl.cJ, wl.cK, grad=g), reps)
+    c64 = ltjk.Context(wl.mol, schwarz_tau=wl.schwarz_tau, precision=ltjk.FP64_NATIVE, device=local)
+    g64 = c64.jk_grad(P, Q, wl.cJ, wl.cK)
+    torch.cuda.synchronize()
+    gmax = float(g64.abs().max())
+    err = float((g - g64).abs().max())
+    st = ctx.stats()
+    return {"workload": wl.name, "terms": int(P.shape[0]), "cJ": wl.cJ, "cK": wl.cK,
+            "grad_ms": ms, "gradients_per_s": 1e3 / ms,
+            "quartets_per_s": st["quartets_kept"] / (ms / 1e3),
+            "max_abs_vs_fp64": err, "rel_to_max_vs_fp64": err / gmax,
+            "sum_over_atoms_rel": float(g.sum(0).abs().max()) / gmax}
+
+
+def measure_macrocycle(ltjk, torch, dev, local, stream, reps=2):
+    """Mixed-precision J/K of 128 pseudo-densities on the 445-AO macrocycle
+    (FP64 for quartets with Q_ab Q_cd > 1e-6): builds/s and the per-element
+    error against the FP64-class build on the same GPU (itself parity-tested
+    against the oracle)."""
+    w = W.config3()
+    mol = w.mol
+    t0 = time.perf_counter()
+    cm = ltjk.Context(mol, schwarz_tau=w.schwarz_tau, mixed_tau=1e-6, precision=ltjk.MIXED, device=local)
+    setup_s = time.perf_counter() - t0
+    xmin = 2.0 * (w.eps_vir.min() - w.eps_occ.max())
+    xmax = 2.0 * (w.eps_vir.max() - w.eps_occ.min())
+    tq, _, _ = ltjk.laplace_quadrature(xmin, xmax, w.nlap)
+    D = cm.pseudo_densities(torch.from_numpy(w.C_occ).to(dev), torch.from_numpy(w.C_vir).to(dev),
+                            torch.from_numpy(w.eps_occ).to(dev), torch.from_numpy(w.eps_vir).to(dev),
+                            torch.from_numpy(np.ascontiguousarray(w.X)).to(dev), tq)
+    J, K = cm.jk_build(D)
+    ms = _event_ms(torch, stream, lambda: cm.jk_build(D, J, K), reps)
+    c64 = ltjk.Context(mol, schwarz_tau=w.schwarz_tau, precision=ltjk.FP64, device=local)
+    J64, K64 = c64.jk_build(D)
+    ms64 = _event_ms(torch, stream, lambda: c64.jk_build(D, J64, K64), 1)
+    dj = float((J - J64).abs().max())
+    dk = float((K - K64).abs().max())
+    st = cm.stats()
+    out = {"workload": w.name, "nao": mol.nao, "ndens": int(D.shape[0]), "precision": "mixed",
+           "mixed_tau": 1e-6, "build_ms": ms, "builds_per_s": D.shape[0] / (ms / 1e3),
+           "fp64_class_builds_per_s": D.shape[0] / (ms64 / 1e3),
+           "quartets_kept": st["quartets_kept"], "quartets_fp64": st["quartets_fp64"],
+           "quartets_per_s": st["quartets_kept"] / (ms / 1e3), "setup_ms": 1e3 * setup_s,
+           "error_vs_fp64_class": {"J_max_abs": dj, "K_max_abs": dk,
+                                   "J_max_rel_to_max": dj / float(J64.abs().max()),
+                                   "K_max_rel_to_max": dk / float(K64.abs().max())}}
+    del cm, c64, D, J, K, J64, K64
+    return out
+
+
 def run_gpu(args, world, rank, local):
     import torch
     from paper_2607_05622_gb300 import ltjk
@@ -312,9 +390,15 @@ def run_gpu(args, world, rank, local):
                "(152 x 128 x 2 x 2070 MHz) by flop share")
     roof = {"bound": "alu", "pipe": pipe,
             "achieved": flops / jk_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-            "frac": flops / jk_s / 1e12 / peak, "traffic": None,
+            "frac": flops / jk_s / 1e12 / peak, "traffic": NCU_DRAM_BYTES_PER_BUILD[args.precision],
+            "traffic_unit": "bytes per build (all class launches of one build)",
+            "algorithmic_bytes_per_build": 3 * nd * N * N * 8,
             "algorithmic_flops_per_build": flops, "peak_source": src,
             "fp32_pipe_peak_tflops": pk["fp32_tflops"], "fp64_pipe_peak_tflops": pk["fp64_tflops"]}
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras["gradient"] = measure_gradient(ltjk, torch, dev, local, stream, prec)
+        extras["macrocycle_445"] = measure_macrocycle(ltjk, torch, dev, local, stream)
     if rank != 0:
         return
     cpu = None
@@ -347,6 +431,7 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    line.update(extras)
     print(json.dumps(line))
 
 
@@ -359,6 +444,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp64-native"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the gradient and 445-AO macrocycle measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
