@@ -11,7 +11,9 @@ Contents (each function cites the passage it follows):
   * the least-squares Laplace quadrature (Eq. laplace), step by step;
   * Laplace pseudo-densities (Eqs. scaledcoeff, aodens/aodensk with R = X);
   * the brute-force energy-denominator sums that the quadrature must reproduce
-    (Eq. factorize).
+    (Eq. factorize);
+  * the Cholesky-factorised two-electron operator and J/K read off it
+    (Eqs. cdfact, cdj, cdknonsym), step by step.
 """
 from __future__ import annotations
 
@@ -380,3 +382,44 @@ def laplace_shift(t, w, omega):
 def laplace_fock(J, K, C_left, C_right, cJ=2.0, cK=-1.0):
     """Eq. laplacefock: F[q] = C_left^T (cJ J[q] + cK K[q]) C_right."""
     return np.einsum("mp,qmn,nr->qpr", C_left, cJ * J + cK * K, C_right, optimize=True)
+
+
+# ------------------------------------------------------------ Cholesky J/K
+def cd_factor(I: np.ndarray, delta: float, max_vectors: int | None = None):
+    """Pivoted incomplete Cholesky factor of the ERI matrix (Eq. cdfact):
+    V[(mu nu), (ka rho)] = (mu nu|ka rho) ~ sum_Q B[Q, mu nu] B[Q, ka rho].
+    The plain algorithm: residual diagonal d = diag(V); while the largest d over
+    the unique pairs mu >= nu exceeds delta, take that pair p, form the new
+    vector (V[:, p] - sum_Q B[Q, :] B[Q, p]) / sqrt(d[p]) and subtract its
+    square from d.  Returns (B [naux, N, N], final max residual diagonal)."""
+    N = I.shape[0]
+    V = I.reshape(N * N, N * N)
+    d = np.diag(V).copy()
+    uniq = np.array([m * N + n for m in range(N) for n in range(m + 1)])
+    vecs = []
+    cap = max_vectors if max_vectors is not None else N * (N + 1) // 2
+    while len(vecs) < cap:
+        p = uniq[np.argmax(d[uniq])]
+        if d[p] <= delta:
+            break
+        col = V[:, p].copy()
+        for v in vecs:
+            col -= v * v[p]
+        v = col / np.sqrt(d[p])
+        vecs.append(v)
+        d -= v * v
+    B = np.array(vecs).reshape(len(vecs), N, N) if vecs else np.zeros((0, N, N))
+    return B, float(d[uniq].max())
+
+
+def cd_jk(B: np.ndarray, U: np.ndarray, V: np.ndarray):
+    """J and K of the densities D[q] = U[q] V[q]^T read off the factor B:
+    J = sum_Q B_Q gamma_Q with gamma_Q = sum B_Q,ka rho D_ka rho (Eq. cdj), and
+    K = sum_{Q,m} (B_Q U)_{mu m} (B_Q V)_{nu m} (Eq. cdknonsym)."""
+    D = np.einsum("qkm,qrm->qkr", U, V)
+    gamma = np.einsum("Qkr,qkr->qQ", B, D)
+    J = np.einsum("qQ,Qmn->qmn", gamma, B)
+    BU = np.einsum("Qmk,qkr->qQmr", B, U)
+    BV = np.einsum("Qmk,qkr->qQmr", B, V)
+    K = np.einsum("qQmr,qQnr->qmn", BU, BV)
+    return J, K
