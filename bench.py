@@ -259,6 +259,63 @@ def measure_macrocycle(ltjk, torch, dev, local, stream, reps=2):
     return out
 
 
+def measure_next_rows(ltjk, torch, stream, ctx, w, J, K, Co, Cv, xmin, xmax, reps=5):
+    """The rows either side of the build: the Laplace-Fock back-transform of the
+    48 J/K pairs to the occupied-virtual block (Eq. laplacefock; FP64 GEMMs on
+    the FP64 pipe) and the host-side minimax grid (Eq. laplace, Remez)."""
+    nd, N = J.shape[0], J.shape[1]
+    no, nv = Co.shape[1], Cv.shape[1]
+    F = torch.empty((nd, no, nv), dtype=torch.float64, device=J.device)
+    ctx.laplace_fock(J, K, Co, Cv, 2.0, -1.0, F=F)
+    ms = _event_ms(torch, stream, lambda: ctx.laplace_fock(J, K, Co, Cv, 2.0, -1.0, F=F), reps)
+    flops = nd * (3.0 * N * N + 2.0 * N * N * nv + 2.0 * N * no * nv)
+    peak = alu_peaks(2070.0)["fp64_tflops"]
+    t0 = time.perf_counter()
+    tm, wm, em, conv = ltjk.laplace_minimax(xmin, xmax, w.nlap)
+    mm_ms = 1e3 * (time.perf_counter() - t0)
+    _, _, els = ltjk.laplace_quadrature(xmin, xmax, w.nlap)
+    return {"laplace_fock": {"densities": nd, "ms": ms, "tflops": flops / (ms / 1e3) / 1e12,
+                             "fp64_pipe_frac": flops / (ms / 1e3) / 1e12 / peak,
+                             "algorithmic_flops": flops},
+            "laplace_minimax": {"points": w.nlap, "host_ms": mm_ms, "max_rel_err": em,
+                                "converged": conv, "least_squares_max_rel_err": els}}
+
+
+def measure_cd(ltjk, torch, stream, ctx, w, D, J, K, Co, Cv, eo, ev, X, t, delta=1e-9, reps=2):
+    """The Cholesky-factorised route on the same request (Eqs. cdfact, cdj,
+    cdknonsym): factor set-up time and vectors, the J/K of the 48 pseudo-densities
+    from their rank-nocc factors, FP64 pipe fraction, and the difference from the
+    direct build (bounded by the residual diagonal times sum|D|)."""
+    N = ctx.nao
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B, naux, res = ctx.cd_factor(delta, 20 * N)
+    torch.cuda.synchronize()
+    factor_s = time.perf_counter() - t0
+    U, V = ctx.pseudo_density_factors(Co, Cv, eo, ev, X, t)
+    U = U[:1].contiguous()  # C_occ: one left factor for every pseudo-density
+    Jc, Kc = ctx.cd_jk(B, U, V)
+    ms = _event_ms(torch, stream, lambda: ctx.cd_jk(B, U, V, J=Jc, K=Kc), reps)
+    nd, r = V.shape[0], V.shape[2]
+    # B U once; per density B V_q, sum_Q (B_Q U)(B_Q V_q)^T, gamma and J
+    flops = 2.0 * naux * N * N * r + nd * (4.0 * naux * N * N * r + 2.0 * naux * N * r + 2.0 * naux * N * N)
+    pk = alu_peaks(2070.0)
+    native = ctx.precision == ltjk.FP64_NATIVE
+    peak = pk["fp64_tflops"] if native else pk["fp32_tflops"] / 2.0 * 2.0 / 15.0
+    dj = float((Jc - J).abs().max())
+    dk = float((Kc - K).abs().max())
+    bound = res * float(D.abs().sum(dim=(1, 2)).max())
+    out = {"delta": delta, "naux": naux, "max_residual": res, "factor_s": factor_s,
+           "jk_ms": ms, "builds_per_s": nd / (ms / 1e3), "rank": r,
+           "tflops": flops / (ms / 1e3) / 1e12, "peak_tflops": peak, "frac": flops / (ms / 1e3) / 1e12 / peak,
+           "arithmetic": "IEEE FP64" if native else "double-float GEMMs on the FP32 pipe",
+           "vs_direct": {"J_max_abs": dj, "K_max_abs": dk, "bound_res_x_sum_abs_D": bound,
+                         "J_max_rel_to_max": dj / float(J.abs().max()),
+                         "K_max_rel_to_max": dk / float(K.abs().max())}}
+    del B, U, V, Jc, Kc
+    return out
+
+
 def run_gpu(args, world, rank, local):
     import torch
     from paper_2607_05622_gb300 import ltjk
@@ -397,6 +454,9 @@ def run_gpu(args, world, rank, local):
             "fp32_pipe_peak_tflops": pk["fp32_tflops"], "fp64_pipe_peak_tflops": pk["fp64_tflops"]}
     extras = {}
     if not args.no_extras and rank == 0:
+        extras["next_rows"] = measure_next_rows(ltjk, torch, stream, ctx, w, J, K, Co, Cv, xmin, xmax)
+        tq, _, _ = ltjk.laplace_quadrature(xmin, xmax, w.nlap)
+        extras["next_rows"]["cholesky_jk"] = measure_cd(ltjk, torch, stream, ctx, w, D, J, K, Co, Cv, eo, ev, X, tq)
         extras["gradient"] = measure_gradient(ltjk, torch, dev, local, stream, prec)
         extras["macrocycle_445"] = measure_macrocycle(ltjk, torch, dev, local, stream)
     if rank != 0:

@@ -245,6 +245,52 @@ int ltjk_laplace_fock(ltjk_ctx *ctx, int ndens, const double *J, const double *K
                       double cK, int nl, const double *C_left, int nr, const double *C_right,
                       double *F, ltjk_stream stream);
 
+/* ----------------------------------------------- Cholesky-factorised J/K */
+/* Pivoted incomplete Cholesky factor of the ERI matrix over AO pairs
+   (Eq. cdfact): (mu nu|ka rho) ~ sum_Q B[Q][mu][nu] B[Q][ka][rho].  Starting
+   from the residual diagonal (mu nu|mu nu), it repeatedly takes the unique
+   pair mu >= nu with the largest residual diagonal (lowest index on ties)
+   while that exceeds delta, evaluates the ERI columns of the pivot's shell
+   pair with the direct build's quartet kernels (IEEE FP64, cached for later
+   pivots of the same pair) and appends the vector
+   (V[:, p] - sum_Q B[Q] B[Q][p]) / sqrt(d_p).  Synchronous.
+     delta > 0, max_vectors >= 1; B [max_vectors][N][N] device, caller-owned
+     (row Q is a symmetric matrix; rows >= *naux are left untouched);
+     *naux receives the number of vectors, *max_residual (nullable) the
+     largest residual diagonal left, which bounds every element of
+     V - B^T B (the residual is positive semidefinite).  The factorisation
+     stops at max_vectors even if the residual is still above delta. */
+int ltjk_cd_factor(ltjk_ctx *ctx, double delta, int max_vectors, double *B, int *naux,
+                   double *max_residual, ltjk_stream stream);
+
+/* J and K of densities given as factors, D[q] = U[q] V[q]^T, read off the
+   Cholesky factor (Eq. cdj: J = sum_Q B_Q gamma_Q, gamma_Q = <B_Q, D>;
+   Eq. cdknonsym: K = sum_{Q,m} (B_Q U)_{mu m} (B_Q V)_{nu m}).  A Laplace
+   pseudo-density D_q = C_occ Y_q C_vir^T has rank nocc with one left factor
+   for all densities: U = C_occ (u_count = 1), V_q = C_vir Y_q^T; a general D
+   is U = D, V = identity (rank N, u_count = ndens).
+   Precision follows the context: IEEE FP64 for LTJK_FP64_NATIVE; otherwise
+   the products B U, B V and sum_Q (B_Q U)(B_Q V)^T run as double-float GEMMs
+   on the FP32 pipe (~2^-44 relative per operation, FP64 accumulation of the
+   split-k partial sums) and J's final contraction in IEEE FP64.
+     B [naux][N][N] from ltjk_cd_factor; U [u_count][N][rank] and
+     V [ndens][N][rank] device, row-major, u_count 1 or ndens; J, K
+     [ndens][N][N] device, overwritten (either may be NULL).
+     1 <= ndens <= 4096, 1 <= rank <= N.  Uses the context's scratch (up to
+     about 2 GB of density chunks plus the left-factor products). */
+int ltjk_cd_jk(ltjk_ctx *ctx, int naux, const double *B, int ndens, int rank, int u_count,
+               const double *U, const double *V, double *J, double *K, ltjk_stream stream);
+
+/* The Laplace pseudo-densities of ltjk_pseudo_densities as rank-nocc factors,
+   D[q*npair + p] = U[q*npair + p] V[q*npair + p]^T with U = C_occ and
+   V = C_vir Y^T, Y = exp(t_q (eps_i - eps_a)) X_p (Eq. scaledcoeff): the
+   input of ltjk_cd_jk.  Arguments as ltjk_pseudo_densities; U, V
+   [nlap*npair][N][nocc] device, overwritten.  Uses the context's scratch. */
+int ltjk_pseudo_density_factors(ltjk_ctx *ctx, int nocc, int nvir, const double *C_occ,
+                                const double *C_vir, const double *eps_occ, const double *eps_vir,
+                                int npair, const double *X, int nlap, const double *t_host, double *U,
+                                double *V, ltjk_stream stream);
+
 /* ------------------------------------------------------------- inspection */
 /* Contracted Cartesian integral blocks of nq shell quartets (a,b|c,d) given in
    shells_host[4*nq]; out [sum of block sizes] device FP64, blocks concatenated

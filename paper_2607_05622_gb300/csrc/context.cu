@@ -1032,4 +1032,5 @@ extern "C" int ltjk_jk_build_noalloc(ltjk_ctx *ctx, int ndens, const double *D, 
   return LTJK_OK;
 }
 
+#include "cholesky.cuh"
 #include "service.cuh"

@@ -86,6 +86,9 @@ SIGNATURES = {
     "ltjk_jk_grad": ([_P, _I, _P, _P, _D, _D, _P, _P], _I),
     "ltjk_shell_quartets": ([_P, _I, _P, _I, _P, _P], _I),
     "ltjk_class_program": ([_I, _I, _I, _I, _I, _P], _I),
+    "ltjk_cd_factor": ([_P, ctypes.c_double, _I, _P, _P, _P, _P], _I),
+    "ltjk_cd_jk": ([_P, _I, _P, _I, _I, _I, _P, _P, _P, _P, _P], _I),
+    "ltjk_pseudo_density_factors": ([_P, _I, _I, _P, _P, _P, _P, _I, _P, _I, _P, _P, _P, _P], _I),
     "ltjk_laplace_fock": ([_P, _I, _P, _P, _D, _D, _I, _P, _I, _P, _P, _P], _I),
     "ltjk_service_create": ([ctypes.c_size_t, _I, _P], _I),
     "ltjk_service_submit": ([_P, _P, _P], _I),
@@ -274,6 +277,48 @@ class Context:
             _dev(X, (npair, no, nv), "X"), nlap, t.ctypes.data_as(_P),
             _dev(D, (nlap * npair, N, N), "D"), _stream(stream)))
         return D
+
+    def cd_factor(self, delta: float, max_vectors: int, stream=None):
+        """ltjk_cd_factor (Eq. cdfact): (B [naux][N][N] view of a [max_vectors][N][N]
+        buffer, naux, largest residual diagonal)."""
+        N = self.nao
+        buf = torch.empty((int(max_vectors), N, N), dtype=torch.float64, device=f"cuda:{self.device}")
+        naux = ctypes.c_int(0)
+        res = ctypes.c_double(0.0)
+        _check(lib().ltjk_cd_factor(self._h, float(delta), int(max_vectors), _dev(buf, name="B"),
+                                    ctypes.byref(naux), ctypes.byref(res), _stream(stream)))
+        return buf[: naux.value], naux.value, res.value
+
+    def pseudo_density_factors(self, C_occ, C_vir, eps_occ, eps_vir, X, t, stream=None):
+        """ltjk_pseudo_density_factors: (U, V) [nlap*npair][N][nocc] with D = U V^T."""
+        N = self.nao
+        no, nv = C_occ.shape[1], C_vir.shape[1]
+        npair = X.shape[0]
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        nq = t.shape[0] * npair
+        U = torch.empty((nq, N, no), dtype=torch.float64, device=C_occ.device)
+        V = torch.empty_like(U)
+        _check(lib().ltjk_pseudo_density_factors(
+            self._h, no, nv, _dev(C_occ, (N, no), "C_occ"), _dev(C_vir, (N, nv), "C_vir"),
+            _dev(eps_occ, (no,), "eps_occ"), _dev(eps_vir, (nv,), "eps_vir"), npair,
+            _dev(X, (npair, no, nv), "X"), t.shape[0], t.ctypes.data_as(_P), _dev(U, name="U"),
+            _dev(V, name="V"), _stream(stream)))
+        return U, V
+
+    def cd_jk(self, B: torch.Tensor, U: torch.Tensor, V: torch.Tensor, J=None, K=None, stream=None):
+        """ltjk_cd_jk (Eqs. cdj, cdknonsym): J and K of D[q] = U[q] V[q]^T from the
+        factor B; U may hold one left factor shared by every density ([1][N][rank])."""
+        naux, N = B.shape[0], self.nao
+        nd, _, rank = V.shape
+        nu = U.shape[0]
+        if J is None:
+            J = torch.empty((nd, N, N), dtype=torch.float64, device=V.device)
+        if K is None:
+            K = torch.empty((nd, N, N), dtype=torch.float64, device=V.device)
+        _check(lib().ltjk_cd_jk(self._h, naux, _dev(B, (naux, N, N), "B"), nd, rank, nu,
+                                _dev(U, (nu, N, rank), "U"), _dev(V, (nd, N, rank), "V"),
+                                _dev(J, (nd, N, N), "J"), _dev(K, (nd, N, N), "K"), _stream(stream)))
+        return J, K
 
     def laplace_fock(self, J, K, C_left, C_right, cJ=2.0, cK=-1.0, F=None, stream=None):
         """F[q] = C_left^T (cJ J[q] + cK K[q]) C_right (Eq. laplacefock)."""
