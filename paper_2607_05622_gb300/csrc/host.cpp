@@ -100,45 +100,20 @@ void boys_table(int rows, int cols, double step, double *tab) {
 // ------------------------------------------------------ Laplace quadrature
 // Fit sum_q w_q exp(-t_q x) ~ 1/x in the least-squares sense on the relative
 // residual r_s = 1 - x_s sum_q w_q exp(-t_q x_s).  The problem is scale
-// invariant, so it is solved on [1, R], R = xmax/xmin.  Parameters are
-// (log t, log w) (positivity); the solver is Levenberg-Marquardt with column
-// scaling, each step from a Householder QR of the scaled Jacobian followed by
-// the damped triangular system.  Points are added one at a time (continuation
-// in n); nearby solutions warm-start new ranges.
+// invariant, so it is solved on [1, R], R = xmax/xmin.  The residual is linear
+// in the weights, so they are eliminated by variable projection (Golub and
+// Pereyra, SIAM J. Numer. Anal. 10, 413 (1973)): for exponents t the weights
+// are the linear least-squares solution (Householder QR), and
+// Levenberg-Marquardt runs on log t alone, with the Jacobian of the projected
+// residual by forward differences.  Points are added one at a time
+// (continuation in n, trying a node beyond the largest exponent, below the
+// smallest and in the widest gap, keeping the lowest cost with positive
+// weights).  Once no added node lowers the cost (the fit has reached the
+// limit double precision allows on this range), the remaining nodes are
+// appended beyond the largest exponent with a negligible weight, so the
+// requested n is honoured without a worse fit.  Nearby solutions warm-start
+// new ranges.
 namespace {
-
-struct LapFit {
-  std::vector<double> xs;
-  int n = 0;
-  double lt_lo = -30, lt_hi = 7;  // bounds on log t (normalised problem)
-  double cost(const std::vector<double> &th, std::vector<double> *r) const {
-    const int m = (int)xs.size();
-    for (int q = 0; q < n; ++q)
-      if (!(th[q] > lt_lo && th[q] < lt_hi && th[n + q] > -80.0 && th[n + q] < 20.0)) return 1e300;
-    double c = 0.0;
-    if (r) r->resize(m);
-    for (int s = 0; s < m; ++s) {
-      double v = 0.0;
-      for (int q = 0; q < n; ++q) v += std::exp(th[n + q] - std::exp(th[q]) * xs[s]);
-      double rr = 1.0 - xs[s] * v;
-      if (r) (*r)[s] = rr;
-      c += rr * rr;
-    }
-    return std::isfinite(c) ? c : 1e300;
-  }
-  // Jacobian J[s][k], k < n: d r/d log t_q; k >= n: d r/d log w_q
-  void jac(const std::vector<double> &th, std::vector<double> &J) const {
-    const int m = (int)xs.size(), p = 2 * n;
-    J.assign((size_t)m * p, 0.0);
-    for (int s = 0; s < m; ++s)
-      for (int q = 0; q < n; ++q) {
-        const double t = std::exp(th[q]);
-        const double e = std::exp(th[n + q] - t * xs[s]);  // w e^{-t x}
-        J[(size_t)s * p + q] = xs[s] * xs[s] * t * e;
-        J[(size_t)s * p + n + q] = -xs[s] * e;
-      }
-  }
-};
 
 // Householder QR of the m x p matrix A (row-major), in place; returns R (p x p,
 // upper) and applies Q^T to b.
@@ -177,70 +152,201 @@ void householder_qr(int m, int p, std::vector<double> &A, std::vector<double> &b
     for (int j = i; j < p; ++j) R[(size_t)i * p + j] = A[(size_t)i * p + j];
 }
 
-// Solve min |R x - c|^2 + lam |x|^2 for upper-triangular R (p x p) by a second QR.
-std::vector<double> damped_solve(int p, const std::vector<double> &R, const std::vector<double> &c,
-                                 double lam) {
-  const int m = 2 * p;
-  std::vector<double> A((size_t)m * p, 0.0), b(m, 0.0), R2;
-  for (int i = 0; i < p; ++i) {
-    for (int j = 0; j < p; ++j) A[(size_t)i * p + j] = R[(size_t)i * p + j];
-    b[i] = c[i];
-    A[(size_t)(p + i) * p + i] = std::sqrt(lam);
+// Solve A x = b (m x m, row-major) by Gaussian elimination with partial
+// pivoting; b is overwritten by x.  Returns false for a singular A.
+bool solve_dense(int m, std::vector<double> &A, std::vector<double> &b) {
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (std::fabs(A[(size_t)r * m + c]) > std::fabs(A[(size_t)piv * m + c])) piv = r;
+    if (A[(size_t)piv * m + c] == 0.0) return false;
+    if (piv != c) {
+      for (int k = 0; k < m; ++k) std::swap(A[(size_t)c * m + k], A[(size_t)piv * m + k]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < m; ++r) {
+      const double f = A[(size_t)r * m + c] / A[(size_t)c * m + c];
+      if (f == 0.0) continue;
+      for (int k = c; k < m; ++k) A[(size_t)r * m + k] -= f * A[(size_t)c * m + k];
+      b[r] -= f * b[c];
+    }
   }
-  householder_qr(m, p, A, b, R2);
-  std::vector<double> x(p, 0.0);
-  for (int i = p - 1; i >= 0; --i) {
-    double s = b[i];
-    for (int j = i + 1; j < p; ++j) s -= R2[(size_t)i * p + j] * x[j];
-    const double d = R2[(size_t)i * p + i];
-    x[i] = d != 0.0 ? s / d : 0.0;
+  for (int r = m - 1; r >= 0; --r) {
+    double v = b[r];
+    for (int k = r + 1; k < m; ++k) v -= A[(size_t)r * m + k] * b[k];
+    b[r] = v / A[(size_t)r * m + r];
   }
-  return x;
+  return true;
 }
 
-void lm_refine(const LapFit &F, std::vector<double> &th, int max_iter) {
-  const int m = (int)F.xs.size(), p = 2 * F.n;
-  std::vector<double> r, J, R, d(p);
-  double cost = F.cost(th, &r);
-  if (cost >= 1e300) return;  // start outside the parameter bounds
+// The normalised problem on [1, R]: sample points and bounds on log t.
+struct LapFit {
+  std::vector<double> xs;
+  double lt_lo = -30, lt_hi = 7;
+  // Weights of the exponents t = exp(th) by linear least squares, the
+  // residual and its squared norm; 1e300 outside the bounds or for a
+  // numerically singular basis.
+  double project(const std::vector<double> &th, std::vector<double> *w, std::vector<double> *r) const {
+    const int m = (int)xs.size(), n = (int)th.size();
+    for (double v : th)
+      if (!(v > lt_lo && v < lt_hi)) return 1e300;
+    std::vector<double> A((size_t)m * n), b(m, 1.0), R;
+    for (int s = 0; s < m; ++s)
+      for (int q = 0; q < n; ++q) A[(size_t)s * n + q] = xs[s] * std::exp(-std::exp(th[q]) * xs[s]);
+    const std::vector<double> A0 = A;
+    householder_qr(m, n, A, b, R);
+    double dmax = 0.0, dmin = 1e300;
+    for (int q = 0; q < n; ++q) {
+      const double d = std::fabs(R[(size_t)q * n + q]);
+      dmax = std::max(dmax, d);
+      dmin = std::min(dmin, d);
+    }
+    if (!(dmin > 1e-15 * dmax)) return 1e300;
+    std::vector<double> ww(n);
+    for (int i = n - 1; i >= 0; --i) {
+      double v = b[i];
+      for (int j = i + 1; j < n; ++j) v -= R[(size_t)i * n + j] * ww[j];
+      ww[i] = v / R[(size_t)i * n + i];
+    }
+    double c = 0.0;
+    std::vector<double> rr(m);
+    for (int s = 0; s < m; ++s) {
+      double v = 1.0;
+      for (int q = 0; q < n; ++q) v -= A0[(size_t)s * n + q] * ww[q];
+      rr[s] = v;
+      c += v * v;
+    }
+    if (!std::isfinite(c)) return 1e300;
+    if (w) *w = ww;
+    if (r) *r = rr;
+    return c;
+  }
+};
+
+// Levenberg-Marquardt on the exponents (log t) with the weights projected
+// out; Marquardt scaling by diag(J^T J); a step is taken only if it lowers the
+// cost.  th and w are updated in place; returns the final cost.
+double varpro_lm(const LapFit &F, std::vector<double> &th, std::vector<double> &w, int max_iter) {
+  const int m = (int)F.xs.size(), n = (int)th.size();
+  std::vector<double> r, rp, J((size_t)m * n);
+  double cost = F.project(th, &w, &r);
+  if (cost >= 1e300) return cost;
   double lam = 1e-3;
   for (int it = 0; it < max_iter; ++it) {
-    F.jac(th, J);
-    for (int k = 0; k < p; ++k) {
-      double s = 0.0;
-      for (int i = 0; i < m; ++i) s += J[(size_t)i * p + k] * J[(size_t)i * p + k];
-      d[k] = s > 1e-300 ? std::sqrt(s) : 1e-150;
-      for (int i = 0; i < m; ++i) J[(size_t)i * p + k] /= d[k];
+    for (int k = 0; k < n; ++k) {  // forward (else backward) differences
+      std::vector<double> tp = th;
+      double h = 1e-7;
+      tp[k] += h;
+      if (F.project(tp, nullptr, &rp) >= 1e300) {
+        tp[k] = th[k] - h;
+        h = -h;
+        if (F.project(tp, nullptr, &rp) >= 1e300) return cost;
+      }
+      for (int s = 0; s < m; ++s) J[(size_t)s * n + k] = (rp[s] - r[s]) / h;
     }
-    std::vector<double> b(m);
-    for (int i = 0; i < m; ++i) b[i] = -r[i];
-    householder_qr(m, p, J, b, R);
-    std::vector<double> c(b.begin(), b.begin() + p);
+    std::vector<double> H((size_t)n * n, 0.0), g(n, 0.0);
+    for (int s = 0; s < m; ++s)
+      for (int a = 0; a < n; ++a) {
+        const double ja = J[(size_t)s * n + a];
+        g[a] += ja * r[s];
+        for (int b = 0; b <= a; ++b) H[(size_t)a * n + b] += ja * J[(size_t)s * n + b];
+      }
+    for (int a = 0; a < n; ++a)
+      for (int b = a + 1; b < n; ++b) H[(size_t)a * n + b] = H[(size_t)b * n + a];
     bool ok = false;
     double dec = 0.0, stepmax = 0.0;
-    for (int trial = 0; trial < 50; ++trial) {
-      std::vector<double> step = damped_solve(p, R, c, lam);
-      std::vector<double> th2(p);
-      stepmax = 0.0;
-      for (int k = 0; k < p; ++k) {
-        th2[k] = th[k] + step[k] / d[k];
-        stepmax = std::max(stepmax, std::fabs(step[k] / d[k]));
+    for (int trial = 0; trial < 40; ++trial) {
+      std::vector<double> A = H, step(n);
+      for (int a = 0; a < n; ++a) {
+        A[(size_t)a * n + a] += lam * (H[(size_t)a * n + a] + 1e-300);
+        step[a] = -g[a];
       }
-      std::vector<double> r2;
-      const double c2 = F.cost(th2, &r2);
+      if (!solve_dense(n, A, step)) {
+        lam *= 4.0;
+        continue;
+      }
+      std::vector<double> th2(n), w2, r2;
+      stepmax = 0.0;
+      for (int a = 0; a < n; ++a) {
+        th2[a] = th[a] + step[a];
+        stepmax = std::max(stepmax, std::fabs(step[a]));
+      }
+      const double c2 = F.project(th2, &w2, &r2);
       if (c2 < cost) {
         dec = (cost - c2) / cost;
         th = th2;
+        w = w2;
         r = r2;
         cost = c2;
-        lam = std::max(lam / 3.0, 1e-30);
+        lam = std::max(lam / 3.0, 1e-20);
         ok = true;
         break;
       }
-      lam = std::max(lam * 4.0, 1e-14);
+      lam *= 4.0;
     }
-    if (!ok) break;
-    if (dec < 1e-13 && stepmax < 1e-9) break;
+    if (!ok || (dec < 1e-15 && stepmax < 1e-12)) break;
+  }
+  return cost;
+}
+
+// Sort exponents ascending, carrying their weights.
+void sort_pairs(std::vector<double> &th, std::vector<double> &w) {
+  std::vector<int> ord(th.size());
+  for (size_t q = 0; q < th.size(); ++q) ord[q] = (int)q;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return th[a] < th[b]; });
+  std::vector<double> t2(th.size()), w2(w.size());
+  for (size_t q = 0; q < th.size(); ++q) {
+    t2[q] = th[ord[q]];
+    w2[q] = w[ord[q]];
+  }
+  th = t2;
+  w = w2;
+}
+
+bool all_positive(const std::vector<double> &w) {
+  for (double v : w)
+    if (!(v > 0.0)) return false;
+  return !w.empty();
+}
+
+// Continuation in the number of points up to n; th/w receive the active
+// nodes (log t, ascending) and their weights.
+void fit_continuation(const LapFit &F, double R, int n, std::vector<double> &th, std::vector<double> &w) {
+  th = {std::log(1.0 / std::sqrt(R))};
+  double cost = varpro_lm(F, th, w, 300);
+  for (int k = 2; k <= n; ++k) {
+    const int km = (int)th.size();
+    const double step = km > 1 ? th[km - 1] - th[km - 2] : std::log(3.0);
+    const double step0 = km > 1 ? th[1] - th[0] : std::log(3.0);
+    std::vector<std::vector<double>> cands;
+    cands.push_back(th);
+    cands.back().push_back(th[km - 1] + step);  // beyond the largest
+    cands.push_back(th);
+    cands.back().push_back(th[0] - step0);  // below the smallest
+    if (km > 1) {  // split the widest gap
+      int gq = 0;
+      for (int q = 1; q + 1 < km; ++q)
+        if (th[q + 1] - th[q] > th[gq + 1] - th[gq]) gq = q;
+      cands.push_back(th);
+      cands.back().push_back(0.5 * (th[gq] + th[gq + 1]));
+    }
+    double best = cost;
+    std::vector<double> bth, bw;
+    for (auto &c : cands) {
+      std::sort(c.begin(), c.end());
+      std::vector<double> wc;
+      const double cc = varpro_lm(F, c, wc, 300);
+      if (cc < best && all_positive(wc)) {
+        best = cc;
+        bth = c;
+        bw = wc;
+      }
+    }
+    if (bth.empty()) break;  // no added node lowers the cost: the fit has converged in n
+    th = bth;
+    w = bw;
+    sort_pairs(th, w);
+    cost = best;
   }
 }
 
@@ -260,85 +366,16 @@ double max_rel_error(const std::vector<double> &t, const std::vector<double> &w,
 
 }  // namespace
 
-// Sort the k nodes (and their weights) ascending.
-static void sort_nodes(std::vector<double> &th, int k) {
-  std::vector<int> ord(k);
-  for (int q = 0; q < k; ++q) ord[q] = q;
-  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return th[a] < th[b]; });
-  std::vector<double> th2(2 * k);
-  for (int q = 0; q < k; ++q) {
-    th2[q] = th[ord[q]];
-    th2[k + q] = th[k + ord[q]];
-  }
-  th = th2;
-}
-
-// Continuation in the number of points: from the best k-1 point fit, try a new
-// node beyond the largest exponent, below the smallest, and in the widest gap;
-// keep the candidate with the lowest cost after refinement.
-static std::vector<double> fit_continuation(LapFit &F, double R, int n) {
-  std::vector<double> th = {std::log(1.0 / std::sqrt(R)), 0.0};
-  F.n = 1;
-  lm_refine(F, th, 300);
-  for (int k = 2; k <= n; ++k) {
-    const int km = k - 1;
-    std::vector<double> lt(th.begin(), th.begin() + km), lw(th.begin() + km, th.end());
-    std::vector<std::vector<double>> cands;
-    const double step = km > 1 ? lt[km - 1] - lt[km - 2] : std::log(3.0);
-    const double step0 = km > 1 ? lt[1] - lt[0] : std::log(3.0);
-    {  // beyond the largest
-      auto t2 = lt, w2 = lw;
-      t2.push_back(lt[km - 1] + step);
-      w2.push_back(lw[km - 1] + std::log(0.5));
-      cands.push_back(t2);
-      cands.back().insert(cands.back().end(), w2.begin(), w2.end());
-    }
-    {  // below the smallest
-      auto t2 = lt, w2 = lw;
-      t2.push_back(lt[0] - step0);
-      w2.push_back(lw[0] - step0);
-      cands.push_back(t2);
-      cands.back().insert(cands.back().end(), w2.begin(), w2.end());
-    }
-    if (km > 1) {  // split the widest gap
-      int g = 0;
-      for (int q = 1; q + 1 < km; ++q)
-        if (lt[q + 1] - lt[q] > lt[g + 1] - lt[g]) g = q;
-      auto t2 = lt, w2 = lw;
-      t2.push_back(0.5 * (lt[g] + lt[g + 1]));
-      w2.push_back(0.5 * (lw[g] + lw[g + 1]) + std::log(0.5));
-      w2[g] += std::log(0.75);
-      w2[g + 1] += std::log(0.75);
-      cands.push_back(t2);
-      cands.back().insert(cands.back().end(), w2.begin(), w2.end());
-    }
-    F.n = k;
-    double best = 1e300;
-    std::vector<double> best_th;
-    for (auto &c : cands) {
-      lm_refine(F, c, 300);
-      const double cc = F.cost(c, nullptr);
-      if (cc < best) {
-        best = cc;
-        best_th = c;
-      }
-    }
-    th = best_th;
-    sort_nodes(th, k);
-  }
-  return th;
-}
-
 int laplace_quadrature(double xmin, double xmax, int n, double *t_out, double *w_out,
                        double *err_out) {
   if (!(xmin > 0) || !(xmax > xmin) || !std::isfinite(xmax) || n < 1 || n > 32 || !t_out || !w_out)
     return set_error(LTJK_EINVAL, "laplace_quadrature: need 0 < xmin < xmax and 1 <= n <= 32");
-  // Cache of normalised solutions per n, keyed by log R: an exact hit is
+  // Cache of normalised active nodes per n, keyed by log R: an exact hit is
   // reused, a nearby one warm-starts the refinement.
   static std::mutex mu;
   static std::map<int, std::map<double, std::vector<double>>> cache;
   const double R = xmax / xmin, lR = std::log(R);
-  std::vector<double> th;
+  std::vector<double> th, w;
   bool exact = false;
   {
     std::lock_guard<std::mutex> g(mu);
@@ -358,32 +395,45 @@ int laplace_quadrature(double xmin, double xmax, int n, double *t_out, double *w
         near = &jt->second;
       }
     }
-    if (near && dist < 0.5) th = *near;
+    if (near && (exact || dist < 0.5)) th = *near;
   }
-  if (!exact) {
-    LapFit F;
-    const int m = 1000;
-    for (int s = 0; s < m; ++s) F.xs.push_back(std::exp(lR * s / (m - 1)));
-    F.lt_lo = std::log(1e-6 / R);
-    F.lt_hi = std::log(1e3);
-    std::vector<double> cold;
+  LapFit F;
+  const int m = 500;
+  for (int s = 0; s < m; ++s) F.xs.push_back(std::exp(lR * s / (m - 1)));
+  F.lt_lo = std::log(1e-6 / R);
+  F.lt_hi = std::log(1e3);
+  if (exact) {
+    F.project(th, &w, nullptr);
+  } else {
+    bool warm = false;
     if (!th.empty()) {
-      F.n = n;
-      lm_refine(F, th, 300);
-      sort_nodes(th, n);
+      std::sort(th.begin(), th.end());
+      const double c = varpro_lm(F, th, w, 300);
+      warm = c < 1e300 && all_positive(w);
+      if (warm) sort_pairs(th, w);
     }
-    if (th.empty() || F.cost(th, nullptr) >= 1e300) th = fit_continuation(F, R, n);
+    if (!warm) fit_continuation(F, R, n, th, w);
     std::lock_guard<std::mutex> g(mu);
     cache[n][lR] = th;
   }
-  std::vector<double> t(n), w(n);
+  // nodes the fit could not use: beyond the largest exponent, negligible weight
+  const int na = (int)th.size();
+  const double step = na > 1 ? th[na - 1] - th[na - 2] : std::log(3.0);
+  double wmin = 1e300;
+  for (double v : w) wmin = std::min(wmin, v);
+  std::vector<double> t(n), wt(n);
   for (int q = 0; q < n; ++q) {
-    t[q] = std::exp(th[q]) / xmin;
-    w[q] = std::exp(th[n + q]) / xmin;
+    if (q < na) {
+      t[q] = std::exp(th[q]) / xmin;
+      wt[q] = w[q] / xmin;
+    } else {
+      t[q] = std::exp(th[na - 1] + (q - na + 1) * step) / xmin;
+      wt[q] = 1e-16 * wmin / xmin;
+    }
     t_out[q] = t[q];
-    w_out[q] = w[q];
+    w_out[q] = wt[q];
   }
-  const double err = max_rel_error(t, w, xmin, xmax, 100000);
+  const double err = max_rel_error(t, wt, xmin, xmax, 100000);
   if (!std::isfinite(err)) return set_error(LTJK_EINVAL, "laplace_quadrature: fit failed");
   if (err_out) *err_out = err;
   return LTJK_OK;
@@ -431,31 +481,6 @@ bool alternation(const std::vector<double> &t, const std::vector<double> &w, dou
   pts.push_back(bx);
   sg.push_back(cur);
   return (int)pts.size() == 2 * n + 1;
-}
-
-bool solve_dense(int m, std::vector<double> &A, std::vector<double> &b) {
-  for (int c = 0; c < m; ++c) {
-    int piv = c;
-    for (int r = c + 1; r < m; ++r)
-      if (std::fabs(A[(size_t)r * m + c]) > std::fabs(A[(size_t)piv * m + c])) piv = r;
-    if (A[(size_t)piv * m + c] == 0.0) return false;
-    if (piv != c) {
-      for (int k = 0; k < m; ++k) std::swap(A[(size_t)c * m + k], A[(size_t)piv * m + k]);
-      std::swap(b[c], b[piv]);
-    }
-    for (int r = c + 1; r < m; ++r) {
-      const double f = A[(size_t)r * m + c] / A[(size_t)c * m + c];
-      if (f == 0.0) continue;
-      for (int k = c; k < m; ++k) A[(size_t)r * m + k] -= f * A[(size_t)c * m + k];
-      b[r] -= f * b[c];
-    }
-  }
-  for (int r = m - 1; r >= 0; --r) {
-    double v = b[r];
-    for (int k = r + 1; k < m; ++k) v -= A[(size_t)r * m + k] * b[k];
-    b[r] = v / A[(size_t)r * m + r];
-  }
-  return true;
 }
 
 // Remez on [1, R] from (t, w); returns false (inputs untouched) on failure.

@@ -64,7 +64,10 @@ def test_library_laplace_quadrature(L, oracle):
             assert err < prev
         prev = err
     _, _, e8 = L.laplace_quadrature(xmin, xmax, 8)
-    assert e8 < 1e-5  # stated accuracy of the library fit at n = 8 (see DESIGN)
+    # the variable-projection fit reaches the oracle's least-squares optimum
+    # (MINPACK on all 2n parameters) within a small factor
+    _, _, eo8 = oracle.laplace_quadrature(xmin, xmax, 8)
+    assert e8 < 1e-7 and e8 <= 10.0 * eo8, (e8, eo8)
     # a cached call returns the same nodes
     t1, w1, _ = L.laplace_quadrature(xmin, xmax, 8)
     t2, w2, _ = L.laplace_quadrature(xmin, xmax, 8)
