@@ -110,8 +110,8 @@ void boys_table(int rows, int cols, double step, double *tab) {
 // smallest and in the widest gap, keeping the lowest cost with positive
 // weights).  Once no added node lowers the cost (the fit has reached the
 // limit double precision allows on this range), the remaining nodes are
-// appended beyond the largest exponent with a negligible weight, so the
-// requested n is honoured without a worse fit.  Nearby solutions warm-start
+// placed in the widest gaps with a negligible weight, so the requested n is
+// honoured without a worse fit.  Nearby solutions warm-start
 // new ranges.
 namespace {
 
@@ -416,20 +416,28 @@ int laplace_quadrature(double xmin, double xmax, int n, double *t_out, double *w
     std::lock_guard<std::mutex> g(mu);
     cache[n][lR] = th;
   }
-  // nodes the fit could not use: beyond the largest exponent, negligible weight
-  const int na = (int)th.size();
-  const double step = na > 1 ? th[na - 1] - th[na - 2] : std::log(3.0);
+  // nodes the fit could not use: at the geometric midpoint of the widest gap
+  // (ordinary exponents, so their pseudo-densities are of ordinary size),
+  // with a weight of 1e-16 of the smallest
   double wmin = 1e300;
   for (double v : w) wmin = std::min(wmin, v);
+  std::vector<double> lt = th, lw = w;
+  while ((int)lt.size() < n) {
+    int g = 0;
+    if (lt.size() > 1) {
+      for (size_t q = 1; q + 1 < lt.size(); ++q)
+        if (lt[q + 1] - lt[q] > lt[g + 1] - lt[g]) g = (int)q;
+      lt.push_back(0.5 * (lt[g] + lt[g + 1]));
+    } else {
+      lt.push_back(lt[0] + std::log(3.0));
+    }
+    lw.push_back(1e-16 * wmin);
+    sort_pairs(lt, lw);
+  }
   std::vector<double> t(n), wt(n);
   for (int q = 0; q < n; ++q) {
-    if (q < na) {
-      t[q] = std::exp(th[q]) / xmin;
-      wt[q] = w[q] / xmin;
-    } else {
-      t[q] = std::exp(th[na - 1] + (q - na + 1) * step) / xmin;
-      wt[q] = 1e-16 * wmin / xmin;
-    }
+    t[q] = std::exp(lt[q]) / xmin;
+    wt[q] = lw[q] / xmin;
     t_out[q] = t[q];
     w_out[q] = wt[q];
   }
