@@ -223,24 +223,29 @@ struct LapFit {
   }
 };
 
-// Levenberg-Marquardt on the exponents (log t) with the weights projected
-// out; Marquardt scaling by diag(J^T J); a step is taken only if it lowers the
-// cost.  th and w are updated in place; returns the final cost.
-double varpro_lm(const LapFit &F, std::vector<double> &th, std::vector<double> &w, int max_iter) {
-  const int m = (int)F.xs.size(), n = (int)th.size();
-  std::vector<double> r, rp, J((size_t)m * n);
-  double cost = F.project(th, &w, &r);
+// Levenberg-Marquardt on the exponents (log t) with the linear unknowns
+// projected out by `proj(th, &lin, &r)` (returns |r|^2, 1e300 when infeasible);
+// Marquardt scaling by diag(J^T J), J by forward differences; a step is taken
+// only if it lowers the cost.  th and lin are updated in place; returns the
+// final cost.
+template <typename Proj>
+double varpro_lm(const Proj &proj, std::vector<double> &th, std::vector<double> &w, int max_iter) {
+  const int n = (int)th.size();
+  std::vector<double> r, rp;
+  double cost = proj(th, &w, &r);
   if (cost >= 1e300) return cost;
+  const int m = (int)r.size();
+  std::vector<double> J((size_t)m * n);
   double lam = 1e-3;
   for (int it = 0; it < max_iter; ++it) {
     for (int k = 0; k < n; ++k) {  // forward (else backward) differences
       std::vector<double> tp = th;
       double h = 1e-7;
       tp[k] += h;
-      if (F.project(tp, nullptr, &rp) >= 1e300) {
+      if (proj(tp, nullptr, &rp) >= 1e300) {
         tp[k] = th[k] - h;
         h = -h;
-        if (F.project(tp, nullptr, &rp) >= 1e300) return cost;
+        if (proj(tp, nullptr, &rp) >= 1e300) return cost;
       }
       for (int s = 0; s < m; ++s) J[(size_t)s * n + k] = (rp[s] - r[s]) / h;
     }
@@ -271,7 +276,7 @@ double varpro_lm(const LapFit &F, std::vector<double> &th, std::vector<double> &
         th2[a] = th[a] + step[a];
         stepmax = std::max(stepmax, std::fabs(step[a]));
       }
-      const double c2 = F.project(th2, &w2, &r2);
+      const double c2 = proj(th2, &w2, &r2);
       if (c2 < cost) {
         dec = (cost - c2) / cost;
         th = th2;
@@ -313,7 +318,10 @@ bool all_positive(const std::vector<double> &w) {
 // nodes (log t, ascending) and their weights.
 void fit_continuation(const LapFit &F, double R, int n, std::vector<double> &th, std::vector<double> &w) {
   th = {std::log(1.0 / std::sqrt(R))};
-  double cost = varpro_lm(F, th, w, 300);
+  auto proj = [&F](const std::vector<double> &x, std::vector<double> *ww, std::vector<double> *rr) {
+    return F.project(x, ww, rr);
+  };
+  double cost = varpro_lm(proj, th, w, 300);
   for (int k = 2; k <= n; ++k) {
     const int km = (int)th.size();
     const double step = km > 1 ? th[km - 1] - th[km - 2] : std::log(3.0);
@@ -335,7 +343,7 @@ void fit_continuation(const LapFit &F, double R, int n, std::vector<double> &th,
     for (auto &c : cands) {
       std::sort(c.begin(), c.end());
       std::vector<double> wc;
-      const double cc = varpro_lm(F, c, wc, 300);
+      const double cc = varpro_lm(proj, c, wc, 300);
       if (cc < best && all_positive(wc)) {
         best = cc;
         bth = c;
@@ -365,6 +373,26 @@ double max_rel_error(const std::vector<double> &t, const std::vector<double> &w,
 }
 
 }  // namespace
+
+// Complete n nodes: the ones a fit could not use go to the geometric midpoint
+// of the widest gap (ordinary exponents, so their pseudo-densities are of
+// ordinary size) with a weight of 1e-16 of the smallest.  lt holds log t.
+static void fill_nodes(std::vector<double> &lt, std::vector<double> &lw, int n) {
+  double wmin = 1e300;
+  for (double v : lw) wmin = std::min(wmin, v);
+  while ((int)lt.size() < n) {
+    int g = 0;
+    if (lt.size() > 1) {
+      for (size_t q = 1; q + 1 < lt.size(); ++q)
+        if (lt[q + 1] - lt[q] > lt[g + 1] - lt[g]) g = (int)q;
+      lt.push_back(0.5 * (lt[g] + lt[g + 1]));
+    } else {
+      lt.push_back(lt[0] + std::log(3.0));
+    }
+    lw.push_back(1e-16 * wmin);
+    sort_pairs(lt, lw);
+  }
+}
 
 int laplace_quadrature(double xmin, double xmax, int n, double *t_out, double *w_out,
                        double *err_out) {
@@ -408,7 +436,10 @@ int laplace_quadrature(double xmin, double xmax, int n, double *t_out, double *w
     bool warm = false;
     if (!th.empty()) {
       std::sort(th.begin(), th.end());
-      const double c = varpro_lm(F, th, w, 300);
+      auto proj = [&F](const std::vector<double> &x, std::vector<double> *ww, std::vector<double> *rr) {
+        return F.project(x, ww, rr);
+      };
+      const double c = varpro_lm(proj, th, w, 300);
       warm = c < 1e300 && all_positive(w);
       if (warm) sort_pairs(th, w);
     }
@@ -416,24 +447,8 @@ int laplace_quadrature(double xmin, double xmax, int n, double *t_out, double *w
     std::lock_guard<std::mutex> g(mu);
     cache[n][lR] = th;
   }
-  // nodes the fit could not use: at the geometric midpoint of the widest gap
-  // (ordinary exponents, so their pseudo-densities are of ordinary size),
-  // with a weight of 1e-16 of the smallest
-  double wmin = 1e300;
-  for (double v : w) wmin = std::min(wmin, v);
   std::vector<double> lt = th, lw = w;
-  while ((int)lt.size() < n) {
-    int g = 0;
-    if (lt.size() > 1) {
-      for (size_t q = 1; q + 1 < lt.size(); ++q)
-        if (lt[q + 1] - lt[q] > lt[g + 1] - lt[g]) g = (int)q;
-      lt.push_back(0.5 * (lt[g] + lt[g + 1]));
-    } else {
-      lt.push_back(lt[0] + std::log(3.0));
-    }
-    lw.push_back(1e-16 * wmin);
-    sort_pairs(lt, lw);
-  }
+  fill_nodes(lt, lw, n);
   std::vector<double> t(n), wt(n);
   for (int q = 0; q < n; ++q) {
     t[q] = std::exp(lt[q]) / xmin;
@@ -491,83 +506,140 @@ bool alternation(const std::vector<double> &t, const std::vector<double> &w, dou
   return (int)pts.size() == 2 * n + 1;
 }
 
+// Lawson's iteration (iteratively reweighted least squares, each sample's
+// weight multiplied by |e(x_s)| after every fit) on the 500-point grid of
+// [1, R]: it moves the least-squares fit towards the best uniform
+// approximation, so that the error acquires the 2n+1 alternating extrema the
+// exchange starts from.  th (log t) and w are updated in place.
+void lawson(double R, std::vector<double> &th, std::vector<double> &w, int iters) {
+  const int m = 500, n = (int)th.size();
+  const double lr = std::log(R), lt_lo = std::log(1e-6 / R), lt_hi = std::log(1e3);
+  std::vector<double> xs(m), om(m, 1.0 / m);
+  for (int s = 0; s < m; ++s) xs[s] = std::exp(lr * s / (m - 1));
+  for (int it = 0; it < iters; ++it) {
+    auto proj = [&](const std::vector<double> &x, std::vector<double> *ww, std::vector<double> *rr) {
+      for (double v : x)
+        if (!(v > lt_lo && v < lt_hi)) return 1e300;
+      std::vector<double> A((size_t)m * n), b(m), Rm;
+      for (int s = 0; s < m; ++s) {
+        const double sq = std::sqrt(om[s]);
+        b[s] = sq;
+        for (int q = 0; q < n; ++q) A[(size_t)s * n + q] = sq * xs[s] * std::exp(-std::exp(x[q]) * xs[s]);
+      }
+      const std::vector<double> A0 = A, b0 = b;
+      householder_qr(m, n, A, b, Rm);
+      double dmax = 0.0, dmin = 1e300;
+      for (int q = 0; q < n; ++q) {
+        dmax = std::max(dmax, std::fabs(Rm[(size_t)q * n + q]));
+        dmin = std::min(dmin, std::fabs(Rm[(size_t)q * n + q]));
+      }
+      if (!(dmin > 1e-15 * dmax)) return 1e300;
+      std::vector<double> sol(n);
+      for (int i = n - 1; i >= 0; --i) {
+        double v = b[i];
+        for (int j = i + 1; j < n; ++j) v -= Rm[(size_t)i * n + j] * sol[j];
+        sol[i] = v / Rm[(size_t)i * n + i];
+      }
+      double c = 0.0;
+      std::vector<double> res(m);
+      for (int s = 0; s < m; ++s) {
+        double v = b0[s];
+        for (int q = 0; q < n; ++q) v -= A0[(size_t)s * n + q] * sol[q];
+        res[s] = v;  // weighted residual
+        c += v * v;
+      }
+      if (!std::isfinite(c)) return 1e300;
+      if (ww) *ww = sol;
+      if (rr) *rr = res;
+      return c;
+    };
+    std::vector<double> th2 = th, w2;
+    if (varpro_lm(proj, th2, w2, 30) >= 1e300 || !all_positive(w2)) return;
+    th = th2;
+    w = w2;
+    double tot = 0.0;
+    for (int s = 0; s < m; ++s) {
+      double v = 0.0;
+      for (int q = 0; q < n; ++q) v += w[q] * std::exp(-std::exp(th[q]) * xs[s]);
+      om[s] *= std::fabs(1.0 - xs[s] * v);
+      tot += om[s];
+    }
+    if (!(tot > 0.0)) return;
+    for (double &v : om) v /= tot;
+  }
+}
+
 // Remez on [1, R] from (t, w); returns false (inputs untouched) on failure.
+// Each exchange solves e(x_i) = s_i E at the 2n+1 alternation points by
+// variable projection: for exponents t the equations are linear in (w, E),
+// solved in the least-squares sense by Householder QR, and Levenberg-Marquardt
+// on log t drives their residual to zero.
 bool remez(double R, int n, std::vector<double> &t, std::vector<double> &w) {
-  std::vector<double> tt = t, ww = w, pts, sg;
+  std::vector<double> th(n), ww = w, pts, sg;
+  for (int q = 0; q < n; ++q) th[q] = std::log(t[q]);
+  lawson(R, th, ww, 20);
+  const double lt_lo = std::log(1e-6 / R), lt_hi = std::log(1e3);
   double emax = 0.0, E = 0.0;
   bool ok = false;
   for (int it = 0; it < 60; ++it) {
+    std::vector<double> tt(n);
+    for (int q = 0; q < n; ++q) tt[q] = std::exp(th[q]);
     if (!alternation(tt, ww, R, n, pts, sg, &emax)) break;
-    E = 0.0;
-    for (int i = 0; i <= 2 * n; ++i) E += std::fabs(rel_err(tt, ww, pts[i]));
-    E /= 2 * n + 1;
-    if (it > 0 && emax <= E * (1.0 + 1e-6)) {
+    if (it > 0 && emax <= std::fabs(E) * (1.0 + 1e-6)) {
       ok = true;
       break;
     }
-    // Newton on F_i = e(x_i) - s_i E over theta = (log t, log w, E)
-    const int m = 2 * n + 1;
-    std::vector<double> th(m);
-    for (int q = 0; q < n; ++q) {
-      th[q] = std::log(tt[q]);
-      th[n + q] = std::log(ww[q]);
-    }
-    th[2 * n] = E;
-    auto resid = [&](const std::vector<double> &x, std::vector<double> &F) {
-      std::vector<double> t2(n), w2(n);
-      for (int q = 0; q < n; ++q) {
-        t2[q] = std::exp(x[q]);
-        w2[q] = std::exp(x[n + q]);
-      }
-      double s = 0.0;
+    const int m = 2 * n + 1, p = n + 1;
+    auto proj = [&](const std::vector<double> &x, std::vector<double> *lin, std::vector<double> *rr) {
+      for (double v : x)
+        if (!(v > lt_lo && v < lt_hi)) return 1e300;
+      std::vector<double> A((size_t)m * p), b(m, 1.0), Rm;
       for (int i = 0; i < m; ++i) {
-        F[i] = rel_err(t2, w2, pts[i]) - sg[i] * x[2 * n];
-        s += F[i] * F[i];
+        for (int q = 0; q < n; ++q) A[(size_t)i * p + q] = pts[i] * std::exp(-std::exp(x[q]) * pts[i]);
+        A[(size_t)i * p + n] = sg[i];
       }
-      return s;
+      const std::vector<double> A0 = A;
+      householder_qr(m, p, A, b, Rm);
+      double dmax = 0.0, dmin = 1e300;
+      for (int q = 0; q < p; ++q) {
+        dmax = std::max(dmax, std::fabs(Rm[(size_t)q * p + q]));
+        dmin = std::min(dmin, std::fabs(Rm[(size_t)q * p + q]));
+      }
+      if (!(dmin > 1e-15 * dmax)) return 1e300;
+      std::vector<double> sol(p);
+      for (int i = p - 1; i >= 0; --i) {
+        double v = b[i];
+        for (int j = i + 1; j < p; ++j) v -= Rm[(size_t)i * p + j] * sol[j];
+        sol[i] = v / Rm[(size_t)i * p + i];
+      }
+      double c = 0.0;
+      std::vector<double> res(m);
+      for (int i = 0; i < m; ++i) {
+        double v = 1.0;
+        for (int q = 0; q < p; ++q) v -= A0[(size_t)i * p + q] * sol[q];
+        res[i] = v;
+        c += v * v;
+      }
+      if (!std::isfinite(c)) return 1e300;
+      if (lin) *lin = sol;
+      if (rr) *rr = res;
+      return c;
     };
-    std::vector<double> F(m);
-    double f0 = resid(th, F);
-    for (int nt = 0; nt < 30 && f0 > 0; ++nt) {
-      std::vector<double> Jm((size_t)m * m), rhs(m);
-      for (int i = 0; i < m; ++i) {
-        const double x = pts[i];
-        for (int q = 0; q < n; ++q) {
-          const double tq = std::exp(th[q]), wq = std::exp(th[n + q]), ex = std::exp(-tq * x);
-          Jm[(size_t)i * m + q] = x * x * wq * tq * ex;  // d e / d log t
-          Jm[(size_t)i * m + n + q] = -x * wq * ex;      // d e / d log w
-        }
-        Jm[(size_t)i * m + 2 * n] = -sg[i];
-        rhs[i] = -F[i];
-      }
-      if (!solve_dense(m, Jm, rhs)) break;
-      double lam = 1.0, f1 = 0.0;
-      std::vector<double> th2(m), F2(m);
-      for (int ls = 0; ls < 30; ++ls, lam *= 0.5) {
-        for (int k = 0; k < m; ++k) th2[k] = th[k] + lam * rhs[k];
-        f1 = resid(th2, F2);
-        if (std::isfinite(f1) && f1 < f0) break;
-      }
-      if (!(std::isfinite(f1) && f1 < f0)) break;
-      th = th2;
-      F = F2;
-      f0 = f1;
-    }
-    for (int q = 0; q < n; ++q) {
-      tt[q] = std::exp(th[q]);
-      ww[q] = std::exp(th[n + q]);
-    }
+    std::vector<double> lin;
+    if (varpro_lm(proj, th, lin, 200) >= 1e300 || lin.size() != (size_t)p) break;
+    ww.assign(lin.begin(), lin.begin() + n);
+    E = lin[n];
+    if (!all_positive(ww)) break;
   }
   if (!ok) return false;
-  for (double v : tt)
-    if (!(v > 0) || !std::isfinite(v)) return false;
-  std::vector<int> ord(n);
-  for (int q = 0; q < n; ++q) ord[q] = q;
-  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return tt[a] < tt[b]; });
+  std::vector<double> tt(n);
   for (int q = 0; q < n; ++q) {
-    t[q] = tt[ord[q]];
-    w[q] = ww[ord[q]];
+    tt[q] = std::exp(th[q]);
+    if (!(tt[q] > 0) || !std::isfinite(tt[q])) return false;
   }
+  sort_pairs(tt, ww);
+  t = tt;
+  w = ww;
   return true;
 }
 
@@ -578,20 +650,28 @@ int laplace_minimax(double xmin, double xmax, int n, double *t_out, double *w_ou
   int rc = laplace_quadrature(xmin, xmax, n, t_out, w_out, nullptr);
   if (rc) return rc;
   const double R = xmax / xmin;
-  std::vector<double> t(n), w(n);
-  for (int q = 0; q < n; ++q) {
-    t[q] = t_out[q] * xmin;
-    w[q] = w_out[q] * xmin;
-  }
-  const bool ok = remez(R, n, t, w);
+  // the exchange runs on the nodes the least-squares fit uses; the others
+  // (negligible weight) are completed afterwards as in the least-squares grid
+  double wmax = 0.0;
+  for (int q = 0; q < n; ++q) wmax = std::max(wmax, w_out[q]);
+  std::vector<double> t, w;
+  for (int q = 0; q < n; ++q)
+    if (w_out[q] > 1e-12 * wmax) {
+      t.push_back(t_out[q] * xmin);
+      w.push_back(w_out[q] * xmin);
+    }
+  const bool ok = remez(R, (int)t.size(), t, w);
   if (converged) *converged = ok ? 1 : 0;
-  std::vector<double> tt(n), wt(n);
-  for (int q = 0; q < n; ++q) {
-    tt[q] = t[q] / xmin;
-    wt[q] = w[q] / xmin;
-    t_out[q] = tt[q];
-    w_out[q] = wt[q];
+  if (ok) {
+    std::vector<double> lt(t.size());
+    for (size_t q = 0; q < t.size(); ++q) lt[q] = std::log(t[q]);
+    fill_nodes(lt, w, n);
+    for (int q = 0; q < n; ++q) {
+      t_out[q] = std::exp(lt[q]) / xmin;
+      w_out[q] = w[q] / xmin;
+    }
   }
+  std::vector<double> tt(t_out, t_out + n), wt(w_out, w_out + n);
   if (err_out) *err_out = max_rel_error(tt, wt, xmin, xmax, 100000);
   return LTJK_OK;
 }
