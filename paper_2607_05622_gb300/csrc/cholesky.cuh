@@ -191,7 +191,9 @@ __global__ void cd_gamma(const double *__restrict__ BU, const double *__restrict
 // product B_flat V^T is stored at C[q][mu][Q][m] (the [mu][(Q,m)] layout that
 // makes (Q, m) one contiguous index of the exchange contraction).  Epilogue
 // ATOMIC: FP64 atomicAdd of the tile into C[i*ldc + c] (split-k partial sums).
-constexpr int kEpiPerm = 0, kEpiAtomic = 1;
+// Epilogue ATOMIC_K: column c = j*N + nu of a chunk of densities stacked along
+// the columns goes to C[j][i][nu] (the exchange matrices of the chunk).
+constexpr int kEpiPerm = 0, kEpiAtomic = 1, kEpiAtomicK = 2;
 struct PermShape {
   int N, naux, r;
 };
@@ -252,6 +254,9 @@ __global__ void __launch_bounds__(256) cd_gemm_nt_df(const double *__restrict__ 
       const double v = to_double(acc[i][j]);
       if (EPI == kEpiAtomic) {
         atomicAdd(C + (size_t)m * ldc + c, v);
+      } else if (EPI == kEpiAtomicK) {
+        const int j = c / ps.N, nu = c - j * ps.N;
+        atomicAdd(C + ((size_t)j * ps.N + m) * ps.N + nu, v);
       } else {
         const long long Q = m / ps.N, mu = m - Q * ps.N;
         const int q = c / ps.r, mm = c - q * ps.r;
@@ -539,11 +544,23 @@ int ltjk_cd_jk(ltjk_ctx *ctx, int naux, const double *B, int ndens, int rank, in
       cd_gamma_perm<<<(int)std::min<long long>(((long long)nc * naux * 32 + 255) / 256, 152 * 32), 256, 0, st>>>(
           BU, u_stride ? blk : 0, V + (size_t)q0 * per, nc, naux, N, rank, gamma + (size_t)q0 * naux);
       g_launches += 3;
-      if (K) {
+      if (K && !u_stride) {
+        // one product for the whole chunk: K[mu][(j, nu)] = sum BU[mu][.] BV_j[nu][.],
+        // the densities stacked along the columns (BV is [j][nu][(Q, m)])
+        CUDA_TRY(cudaMemsetAsync(K + (size_t)q0 * NN, 0, (size_t)nc * NN * sizeof(double), st));
+        const int ctiles = (nc * N + 63) / 64, rtiles = (N + 63) / 64;
+        const int zk = (int)std::max<long long>(1, std::min<long long>((kd + 15) / 16,
+                                                                        (152 * 3 + rtiles * ctiles - 1) / (rtiles * ctiles)));
+        const long long kchunk_c = ((kd + zk - 1) / zk + 15) / 16 * 16;
+        const int gzc = (int)((kd + kchunk_c - 1) / kchunk_c);
+        cd_gemm_nt_df<kEpiAtomicK><<<dim3(rtiles, ctiles, gzc), 256, 0, st>>>(
+            BU, (int)kd, BV, (int)kd, K + (size_t)q0 * NN, N, N, nc * N, kd, kchunk_c, ps);
+        g_launches += 1;
+      } else if (K) {
         for (int j = 0; j < nc; ++j) {
           const int q = q0 + j;
           double *Kq = K + (size_t)q * NN;
-          const double *BUq = BU + (u_stride ? (size_t)j * blk : 0);
+          const double *BUq = BU + (size_t)j * blk;
           CUDA_TRY(cudaMemsetAsync(Kq, 0, NN * sizeof(double), st));
           cd_gemm_nt_df<kEpiAtomic><<<dim3((N + 63) / 64, (N + 63) / 64, gz), 256, 0, st>>>(
               BUq, (int)kd, BV + (size_t)j * blk, (int)kd, Kq, N, N, N, kd, kchunk, ps);
