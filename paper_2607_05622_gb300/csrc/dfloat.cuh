@@ -194,6 +194,49 @@ __device__ __forceinline__ double scale_pow2(double x, float w) { return x * (do
 __device__ __forceinline__ float scale_pow2(float x, float w) { return x * w; }
 __device__ __forceinline__ dflt scale_pow2(dflt x, float w) { return dflt(x.hi * w, x.lo * w); }
 
+// Compensated dot-product accumulator for double-float operands (the
+// accumulation of Ogita, Rump and Oishi's Dot2, SIAM J. Sci. Comput. 26, 1955
+// (2005), with double-float inputs): the product's leading part is exact by
+// FMA TwoProduct, the cross terms join its error, the leading parts are summed
+// with Knuth's TwoSum, and all error terms go to `lo` unnormalised.  The only
+// dependency from one term to the next is one add on hi and one on lo;
+// acc_final renormalises once (~n^2 2^-48 relative for n terms).
+struct DotAcc {
+  float hi, lo;
+};
+template <typename Real>
+struct AccOf {
+  using type = Real;
+};
+template <>
+struct AccOf<dflt> {
+  using type = DotAcc;
+};
+__device__ __forceinline__ double acc_zero(double) { return 0.0; }
+__device__ __forceinline__ float acc_zero(float) { return 0.0f; }
+__device__ __forceinline__ DotAcc acc_zero(dflt) { return DotAcc{0.0f, 0.0f}; }
+__device__ __forceinline__ double acc_fma(double acc, double a, double b) { return ::fma(a, b, acc); }
+__device__ __forceinline__ float acc_fma(float acc, float a, float b) { return ::fmaf(a, b, acc); }
+__device__ __forceinline__ DotAcc acc_fma(DotAcc acc, dflt a, dflt b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float s = __fadd_rn(acc.hi, p);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  return DotAcc{s, __fadd_rn(acc.lo, __fadd_rn(err, e))};
+}
+__device__ __forceinline__ double acc_final(double acc) { return acc; }
+__device__ __forceinline__ double acc_final(float acc) { return f2d_bits(acc); }
+__device__ __forceinline__ double acc_final(DotAcc acc) {
+  // TwoSum renormalisation, then the integer conversion of the pair
+  const float s = __fadd_rn(acc.hi, acc.lo);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(acc.lo, bb));
+  return df_to_double(s, err);
+}
+
 template <typename Real>
 __device__ __forceinline__ Real zero_real() { return Real(0); }
 template <>

@@ -425,7 +425,8 @@ __device__ __forceinline__ const dflt *digest_operand<dflt>(const JKArgs &a, boo
 // u su + v sv] M(u, v), for every output (x, y) of the nout = nr x nc block and
 // every density.  Lanes run over (output group, density) units, four outputs per
 // group sharing each density load (four independent accumulation chains), so a
-// warp stays full when the number of densities is not a multiple of 32.  The
+// warp stays full when the number of densities is not a multiple of 32.
+// Double-float sums use the compensated accumulator (AccOf<dflt>).  The
 // sums stay runtime loops: unrolled per block shape, the double-float code of
 // the ten placements outgrows the instruction cache and stalls every warp on
 // the SM, the recurrence's included.
@@ -449,23 +450,24 @@ __device__ __forceinline__ void digest_place(const Real *__restrict__ I, const R
       Ib[j] = I + x * sr + y * sc;
       to[j] = (size_t)x * mrow + (size_t)y * nd + q;
     }
-    Real acc0 = zero_real<Real>(), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+    using Acc = typename AccOf<Real>::type;
+    Acc acc0 = acc_zero(Real()), acc1 = acc0, acc2 = acc0, acc3 = acc0;
     const Real *Mu = Mblk + q;
     for (int u = 0; u < nu; ++u, Mu += mrow) {
       const int iu = u * su;
       for (int v = 0; v < nv; ++v) {
         const Real m = ldg(Mu + (size_t)v * nd);
         const int iv = iu + v * sv;
-        acc0 = fma(Ib[0][iv], m, acc0);
-        acc1 = fma(Ib[1][iv], m, acc1);
-        acc2 = fma(Ib[2][iv], m, acc2);
-        acc3 = fma(Ib[3][iv], m, acc3);
+        acc0 = acc_fma(acc0, Ib[0][iv], m);
+        acc1 = acc_fma(acc1, Ib[1][iv], m);
+        acc2 = acc_fma(acc2, Ib[2][iv], m);
+        acc3 = acc_fma(acc3, Ib[3][iv], m);
       }
     }
-    atomicAdd(Tblk + to[0], to_double(acc0));
-    if (cnt > 1) atomicAdd(Tblk + to[1], to_double(acc1));
-    if (cnt > 2) atomicAdd(Tblk + to[2], to_double(acc2));
-    if (cnt > 3) atomicAdd(Tblk + to[3], to_double(acc3));
+    atomicAdd(Tblk + to[0], acc_final(acc0));
+    if (cnt > 1) atomicAdd(Tblk + to[1], acc_final(acc1));
+    if (cnt > 2) atomicAdd(Tblk + to[2], acc_final(acc2));
+    if (cnt > 3) atomicAdd(Tblk + to[3], acc_final(acc3));
     q += 32;
     while (q >= nd) { q -= nd; ++grp; }
   }
