@@ -430,13 +430,13 @@ __device__ __forceinline__ const dflt *digest_operand<dflt>(const JKArgs &a, boo
 // sums stay runtime loops: unrolled per block shape, the double-float code of
 // the ten placements outgrows the instruction cache and stalls every warp on
 // the SM, the recurrence's included.
+// tab[grp*4 + j] = (integral offset, output offset without the density) of
+// output j of group grp, tabulated once per quartet by digest_jk.
 template <typename Real>
 __device__ __forceinline__ void digest_place(const Real *__restrict__ I, const Real *__restrict__ Mblk,
                                              double *__restrict__ Tblk, int nd, size_t mrow, int nout,
-                                             int nc, int sr, int sc, int su, int sv, int nu, int nv,
-                                             int lane) {
+                                             const int2 *tab, int su, int sv, int nu, int nv, int lane) {
   const int ngrp = (nout + 3) >> 2;
-  const unsigned inv_nc = (65536u + (unsigned)nc - 1u) / (unsigned)nc;  // o / nc exact for o < 2^10
   int q = lane, grp = 0;
   while (q >= nd) { q -= nd; ++grp; }
   while (grp < ngrp) {
@@ -445,10 +445,9 @@ __device__ __forceinline__ void digest_place(const Real *__restrict__ I, const R
     size_t to[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int o = o0 + (j < cnt ? j : 0);
-      const int x = (int)(((unsigned)o * inv_nc) >> 16), y = o - x * nc;
-      Ib[j] = I + x * sr + y * sc;
-      to[j] = (size_t)x * mrow + (size_t)y * nd + q;
+      const int2 t = tab[o0 + j];
+      Ib[j] = I + t.x;
+      to[j] = (size_t)(unsigned)t.y + q;
     }
     using Acc = typename AccOf<Real>::type;
     Acc acc0 = acc_zero(Real()), acc1 = acc0, acc2 = acc0, acc3 = acc0;
@@ -473,22 +472,46 @@ __device__ __forceinline__ void digest_place(const Real *__restrict__ I, const R
   }
 }
 
+// The ten placements of one quartet.  tab is scratch shared memory of the warp
+// (its primitive table, dead between the recurrences of two kets) for the
+// per-output offsets of every placement: at most 10 x 9 groups x 4 outputs of
+// 8 bytes, 2880 bytes, below the smallest primitive table (32 x 24 FP32 words).
+// The output offsets x*N*nd + y*nd fit 32 bits for every size the build accepts.
 template <typename Real>
 __device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], const int n[4], int N,
-                          int lane) {
+                          int2 *tab, int lane) {
   const int str[4] = {n[1] * n[2] * n[3], n[2] * n[3], n[3], 1};
   const int nd = a.nd;
   const size_t mrow = (size_t)N * nd;  // stride of one AO row in the q-innermost layout
+  int base[11];
+  base[0] = 0;
   for (int pl = 0; pl < 10; ++pl) {
     const Placement P = c_place[pl];
-    if (P.isJ ? a.J == nullptr : a.K == nullptr) continue;
+    const bool on = P.isJ ? a.J != nullptr : a.K != nullptr;
+    base[pl + 1] = base[pl] + (on ? ((n[P.orow] * n[P.ocol] + 3) >> 2) * 4 : 0);
+  }
+  for (int e = lane; e < base[10]; e += 32) {
+    int pl = 0;
+    while (e >= base[pl + 1]) ++pl;
+    const Placement P = c_place[pl];
+    const int r = e - base[pl], o0 = r & ~3, j = r & 3;
+    const int nout = n[P.orow] * n[P.ocol], nc = n[P.ocol];
+    const int o = o0 + (j < min(4, nout - o0) ? j : 0);
+    const int x = o / nc, y = o - x * nc;
+    tab[e] = make_int2(x * str[P.orow] + y * str[P.ocol], (int)((size_t)x * mrow + (size_t)y * nd));
+  }
+  __syncwarp();
+  for (int pl = 0; pl < 10; ++pl) {
+    const Placement P = c_place[pl];
+    if (base[pl + 1] == base[pl]) continue;
     const Real *M = digest_operand<Real>(a, P.isJ);
     double *T = P.isJ ? a.J : a.K;
     const Real *Mblk = M + ((size_t)off[P.srow] * N + off[P.scol]) * nd;
     double *Tblk = T + ((size_t)off[P.orow] * N + off[P.ocol]) * nd;
-    digest_place<Real>(I, Mblk, Tblk, nd, mrow, n[P.orow] * n[P.ocol], n[P.ocol], str[P.orow],
-                       str[P.ocol], str[P.srow], str[P.scol], n[P.srow], n[P.scol], lane);
+    digest_place<Real>(I, Mblk, Tblk, nd, mrow, n[P.orow] * n[P.ocol], tab + base[pl], str[P.srow],
+                       str[P.scol], n[P.srow], n[P.scol], lane);
   }
+  __syncwarp();  // the table region is the next ket's primitive table
 }
 
 // Gamma of one quartet for the gradient: the sum over the distinct images of
@@ -571,7 +594,7 @@ __global__ void __launch_bounds__(128, 4) quartet_kernel(DevProgs PR, ClassLaunc
           Real *Iw = const_cast<Real *>(I);
           for (int t = lane; t < p.nout; t += 32) Iw[t] = scale_pow2(Iw[t], wf);  // degeneracy weight, once
           __syncwarp();
-          digest_jk<Real>(a, I, off, n, N, lane);
+          digest_jk<Real>(a, I, off, n, N, reinterpret_cast<int2 *>(sm), lane);
         } else {
           double v = 0.0;
           for (int e = lane; e < p.nout; e += 32) v = fma(to_double(I[e]), gam[e], v);
