@@ -90,3 +90,41 @@ def test_library_minimax_and_shift(L, oracle):
     assert np.allclose(ws, oracle.laplace_shift(t, w, 0.75), rtol=1e-14, atol=0)
     with pytest.raises(L.LtjkError):
         L.laplace_shift(t, w, float("nan"))
+
+
+def test_library_quadrature_on_the_chain_range(L, oracle):
+    """On the 200-AO chain's denominator range the variable-projection fit keeps
+    improving with n up to the double-precision floor (least squares 4.8e-8 at
+    n = 8, ~2e-10 at n = 16), returns n distinct positive nodes and positive
+    weights, and its reported error is the oracle's measure of the same grid."""
+    from paper_2607_05622_gb300 import workloads as W
+    w = W.config2()
+    xmin, xmax = oracle.laplace_range(w.eps_occ, w.eps_vir)
+    errs = {}
+    for n in (4, 8, 16):
+        t, wq, err = L.laplace_quadrature(xmin, xmax, n)
+        assert t.shape == (n,) and np.all(np.diff(t) > 0) and np.all(wq > 0)
+        assert abs(err - oracle.laplace_error(t, wq, xmin, xmax)) <= 1e-12 + 1e-9 * err
+        errs[n] = err
+    assert errs[8] < 1e-7 and errs[16] < 1e-9 and errs[16] < errs[8] < errs[4]
+
+
+def test_library_minimax_equioscillates_on_the_chain_range(L, oracle):
+    """n = 8 on the 200-AO chain's range: Lawson reweighting plus the exchange
+    converge, the relative error alternates in sign at 2n+1 points with equal
+    magnitude (the characterisation of the best uniform approximation), and it
+    is below the least-squares grid's maximum error."""
+    from paper_2607_05622_gb300 import workloads as W
+    w = W.config2()
+    xmin, xmax = oracle.laplace_range(w.eps_occ, w.eps_vir)
+    t, wq, err, conv = L.laplace_minimax(xmin, xmax, 8)
+    assert conv
+    _, _, els = L.laplace_quadrature(xmin, xmax, 8)
+    assert err < els
+    x = np.geomspace(xmin, xmax, 200001)
+    e = 1.0 - x * (np.exp(-np.outer(x, t)) @ wq)
+    sg = np.sign(e)
+    runs = np.split(np.abs(e), np.nonzero(sg[1:] != sg[:-1])[0] + 1)
+    peaks = np.array([r.max() for r in runs])
+    assert len(peaks) == 17
+    assert peaks.max() <= peaks.min() * (1 + 1e-3)
