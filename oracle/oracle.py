@@ -13,7 +13,8 @@ Contents (each function cites the passage it follows):
   * the brute-force energy-denominator sums that the quadrature must reproduce
     (Eq. factorize);
   * the Cholesky-factorised two-electron operator and J/K read off it
-    (Eqs. cdfact, cdj, cdknonsym), step by step.
+    (Eqs. cdfact, cdj, cdknonsym), step by step;
+  * the Cartesian -> real-spherical transformation of AO matrices.
 """
 from __future__ import annotations
 
@@ -423,3 +424,39 @@ def cd_jk(B: np.ndarray, U: np.ndarray, V: np.ndarray):
     BV = np.einsum("Qmk,qkr->qQmr", B, V)
     K = np.einsum("qQmr,qQnr->qmn", BU, BV)
     return J, K
+
+
+# ------------------------------------------------ spherical (real solid) AOs
+def sph_block(l: int) -> np.ndarray:
+    """Rows: normalised real solid harmonics of one shell in terms of its
+    Cartesian components (descending l_x, then l_y; every component carries the
+    normalisation of x^l).  s: 1; p: x, y, z kept in Cartesian order; d, in the
+    order m = -2..2: sqrt3 xy, sqrt3 yz, (2 zz - xx - yy)/2, sqrt3 xz,
+    sqrt3/2 (xx - yy)."""
+    if l == 0:
+        return np.ones((1, 1))
+    if l == 1:
+        return np.eye(3)
+    if l == 2:
+        r3 = np.sqrt(3.0)
+        #               xx        xy  xz  yy        yz  zz
+        return np.array([[0.0, r3, 0.0, 0.0, 0.0, 0.0],
+                         [0.0, 0.0, 0.0, 0.0, r3, 0.0],
+                         [-0.5, 0.0, 0.0, -0.5, 0.0, 1.0],
+                         [0.0, 0.0, r3, 0.0, 0.0, 0.0],
+                         [r3 / 2, 0.0, 0.0, -r3 / 2, 0.0, 0.0]])
+    raise ValueError("spherical transform defined for l <= 2")
+
+
+def sph_transform(mol) -> np.ndarray:
+    """T [N_sph, N_cart], block diagonal over the shells in input order."""
+    blocks = [sph_block(l) for l in mol.shell_l]
+    ns = sum(b.shape[0] for b in blocks)
+    nc = sum(b.shape[1] for b in blocks)
+    T = np.zeros((ns, nc))
+    r = c = 0
+    for b in blocks:
+        T[r:r + b.shape[0], c:c + b.shape[1]] = b
+        r += b.shape[0]
+        c += b.shape[1]
+    return T
