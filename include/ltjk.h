@@ -245,6 +245,21 @@ int ltjk_laplace_fock(ltjk_ctx *ctx, int ndens, const double *J, const double *K
                       double cK, int nl, const double *C_left, int nr, const double *C_right,
                       double *F, ltjk_stream stream);
 
+/* ------------------------------------------------------ spherical AOs */
+/* Matrix-level Cartesian <-> real-spherical transformation.  The paper works
+   in Cartesian shells (Computational Details); this maps AO matrices to real
+   spherical functions, T block diagonal over the shells: s 1; p x, y, z (the
+   Cartesian order); d, m = -2..2: sqrt3 xy, sqrt3 yz, (2 zz - xx - yy)/2,
+   sqrt3 xz, sqrt3 (xx - yy)/2, with every Cartesian component normalised as
+   x^l.  direction 0: B[q] = T A[q] T^T (A [ndens][N][N] Cartesian, e.g. J
+   or K, to B [ndens][Ns][Ns]); direction 1: B[q] = T^T A[q] T (a spherical
+   density A [ndens][Ns][Ns] to the Cartesian B [ndens][N][N] the build
+   takes).  IEEE FP64, device arrays; uses the context's scratch.
+   ltjk_nsph gives Ns = sum over shells of 2l+1. */
+int ltjk_nsph(const ltjk_ctx *ctx, int *nsph);
+int ltjk_sph_transform(ltjk_ctx *ctx, int direction, int ndens, const double *A, double *B,
+                       ltjk_stream stream);
+
 /* ----------------------------------------------- Cholesky-factorised J/K */
 /* Pivoted incomplete Cholesky factor of the ERI matrix over AO pairs
    (Eq. cdfact): (mu nu|ka rho) ~ sum_Q B[Q][mu][nu] B[Q][ka][rho].  Starting

@@ -254,6 +254,8 @@ struct ltjk_ctx {
   std::vector<std::unique_ptr<ClassWork>> work;       // value build
   std::vector<std::unique_ptr<ClassWork>> work_grad;  // gradient (same screening)
   DevBuf scratch;
+  DevBuf d_sph;   // Cartesian -> real-spherical matrix T [nsph][nao], built on first use
+  int nsph = 0;
   DevBuf d_t;
   ltjk_ctx_stats stats{};
   cudaStream_t side[kSideStreams] = {};
@@ -760,6 +762,79 @@ int ltjk_context_destroy(ltjk_ctx *ctx) {
 int ltjk_nao(const ltjk_ctx *ctx, int *nao) {
   if (!ctx || !nao) return set_error(LTJK_EINVAL, "nao: null argument");
   *nao = ctx->nao;
+  return LTJK_OK;
+}
+
+int ltjk_nsph(const ltjk_ctx *ctx, int *nsph) {
+  if (!ctx || !nsph) return set_error(LTJK_EINVAL, "nsph: null argument");
+  int n = 0;
+  for (int l : ctx->sh_l) n += 2 * l + 1;
+  *nsph = n;
+  return LTJK_OK;
+}
+
+int ltjk_sph_transform(ltjk_ctx *ctx, int direction, int ndens, const double *A, double *B,
+                       ltjk_stream stream) {
+  if (!ctx || !A || !B) return set_error(LTJK_EINVAL, "sph_transform: null argument");
+  if ((direction != 0 && direction != 1) || ndens < 1 || ndens > 4096)
+    return set_error(LTJK_EINVAL, "sph_transform: direction must be 0 or 1 and 1 <= ndens <= 4096");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int Nc = ctx->nao;
+  int rc;
+  if (ctx->nsph == 0) {
+    // T, block diagonal: real solid harmonics of each shell in terms of its
+    // Cartesian components (every component normalised as x^l); p keeps the
+    // Cartesian order x, y, z; d in the order m = -2..2.
+    int Ns = 0;
+    for (int l : ctx->sh_l) Ns += 2 * l + 1;
+    std::vector<double> T((size_t)Ns * Nc, 0.0);
+    const double r3 = std::sqrt(3.0);
+    int row = 0;
+    for (int sh = 0; sh < ctx->nshells; ++sh) {
+      const int l = ctx->sh_l[sh], c0 = ctx->sh_ao[sh];
+      auto at = [&](int r, int c) -> double & { return T[(size_t)(row + r) * Nc + c0 + c]; };
+      if (l == 0) {
+        at(0, 0) = 1.0;
+      } else if (l == 1) {
+        for (int k = 0; k < 3; ++k) at(k, k) = 1.0;
+      } else if (l == 2) {  // components xx, xy, xz, yy, yz, zz
+        at(0, 1) = r3;                   // xy
+        at(1, 4) = r3;                   // yz
+        at(2, 0) = -0.5;                 // (2 zz - xx - yy) / 2
+        at(2, 3) = -0.5;
+        at(2, 5) = 1.0;
+        at(3, 2) = r3;                   // xz
+        at(4, 0) = 0.5 * r3;             // (xx - yy) sqrt3 / 2
+        at(4, 3) = -0.5 * r3;
+      } else {
+        return set_error(LTJK_EUNSUPPORTED, "sph_transform: l = %d", l);
+      }
+      row += 2 * l + 1;
+    }
+    if ((rc = ctx->d_sph.upload(T))) return rc;
+    ctx->nsph = Ns;
+  }
+  const int Ns = ctx->nsph;
+  const double *T = ctx->d_sph.as<double>();
+  if ((rc = ctx->ensure_scratch((size_t)ndens * Ns * Nc * sizeof(double), st))) return rc;
+  double *X = ctx->scratch.as<double>();
+  const dim3 thr(16, 16);
+  if (direction == 0) {
+    // X[q] = T A[q] ([Ns][Nc] x [Nc][Nc]); B[q] = X[q] T^T ([Ns][Nc] x [Nc][Ns])
+    gemm_f64<false><<<dim3((Nc + 15) / 16, (Ns + 15) / 16, ndens), thr, 0, st>>>(
+        T, 0, A, (long long)Nc * Nc, X, (long long)Ns * Nc, Ns, Nc, Nc, Nc, Nc, Nc);
+    gemm_f64<true><<<dim3((Ns + 15) / 16, (Ns + 15) / 16, ndens), thr, 0, st>>>(
+        X, (long long)Ns * Nc, T, 0, B, (long long)Ns * Ns, Ns, Ns, Nc, Nc, Nc, Ns);
+  } else {
+    // X[q] = T^T A[q] ([Nc][Ns] x [Ns][Ns]); B[q] = X[q] T ([Nc][Ns] x [Ns][Nc])
+    gemm_f64<false, true><<<dim3((Ns + 15) / 16, (Nc + 15) / 16, ndens), thr, 0, st>>>(
+        T, 0, A, (long long)Ns * Ns, X, (long long)Nc * Ns, Nc, Ns, Ns, Nc, Ns, Ns);
+    gemm_f64<false><<<dim3((Nc + 15) / 16, (Nc + 15) / 16, ndens), thr, 0, st>>>(
+        X, (long long)Nc * Ns, T, 0, B, (long long)Nc * Nc, Nc, Nc, Ns, Ns, Nc, Nc);
+  }
+  CUDA_TRY(cudaGetLastError());
+  g_launches += 2;
   return LTJK_OK;
 }
 

@@ -86,6 +86,8 @@ SIGNATURES = {
     "ltjk_jk_grad": ([_P, _I, _P, _P, _D, _D, _P, _P], _I),
     "ltjk_shell_quartets": ([_P, _I, _P, _I, _P, _P], _I),
     "ltjk_class_program": ([_I, _I, _I, _I, _I, _P], _I),
+    "ltjk_nsph": ([_P, _P], _I),
+    "ltjk_sph_transform": ([_P, _I, _I, _P, _P, _P], _I),
     "ltjk_cd_factor": ([_P, ctypes.c_double, _I, _P, _P, _P, _P], _I),
     "ltjk_cd_jk": ([_P, _I, _P, _I, _I, _I, _P, _P, _P, _P, _P], _I),
     "ltjk_pseudo_density_factors": ([_P, _I, _I, _P, _P, _P, _P, _I, _P, _I, _P, _P, _P, _P], _I),
@@ -277,6 +279,28 @@ class Context:
             _dev(X, (npair, no, nv), "X"), nlap, t.ctypes.data_as(_P),
             _dev(D, (nlap * npair, N, N), "D"), _stream(stream)))
         return D
+
+    @property
+    def nsph(self) -> int:
+        n = ctypes.c_int()
+        _check(lib().ltjk_nsph(self._h, ctypes.byref(n)))
+        return n.value
+
+    def to_spherical(self, A: torch.Tensor, stream=None):
+        """ltjk_sph_transform direction 0: T A[q] T^T (Cartesian matrices to spherical)."""
+        nd, N, Ns = A.shape[0], self.nao, self.nsph
+        B = torch.empty((nd, Ns, Ns), dtype=torch.float64, device=A.device)
+        _check(lib().ltjk_sph_transform(self._h, 0, nd, _dev(A, (nd, N, N), "A"), _dev(B, name="B"),
+                                        _stream(stream)))
+        return B
+
+    def from_spherical(self, A: torch.Tensor, stream=None):
+        """ltjk_sph_transform direction 1: T^T A[q] T (spherical densities to Cartesian)."""
+        nd, N, Ns = A.shape[0], self.nao, self.nsph
+        B = torch.empty((nd, N, N), dtype=torch.float64, device=A.device)
+        _check(lib().ltjk_sph_transform(self._h, 1, nd, _dev(A, (nd, Ns, Ns), "A"), _dev(B, name="B"),
+                                        _stream(stream)))
+        return B
 
     def cd_factor(self, delta: float, max_vectors: int, stream=None):
         """ltjk_cd_factor (Eq. cdfact): (B [naux][N][N] view of a [max_vectors][N][N]
