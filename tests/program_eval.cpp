@@ -1,0 +1,134 @@
+// Test infrastructure: evaluates contracted Cartesian shell quartets on the CPU
+// by interpreting the library's generated recurrence programs (the programs
+// the integral kernels run: Obara-Saika vertical steps level by level, the
+// accumulation, the horizontal steps and the output block), with this file's
+// own Boys function and primitive set-up.  The tests compare its blocks with
+// the oracle's McMurchie-Davidson blocks, which pins the program generator on
+// the CPU.  Compiled by the test itself (g++), never by the library build.
+#include <cmath>
+#include <vector>
+
+#include "ltjk_internal.h"
+
+using namespace ltjk;
+
+namespace {
+
+const ProgramSet &programs() {
+  static ProgramSet ps;
+  static bool built = false;
+  if (!built) {
+    build_programs(ps);
+    built = true;
+  }
+  return ps;
+}
+
+// F_m(T), m = 0..mmax: the convergent series e^{-T} sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1))
+// evaluated for F_mmax and descended; for large T the erf form and upward recursion.
+void boys(int mmax, double T, double *F) {
+  if (T < 30.0) {
+    long double term = 1.0L / (2 * mmax + 1), sum = term;
+    for (int k = 1; k < 400; ++k) {
+      term *= 2.0L * T / (2 * mmax + 2 * k + 1);
+      sum += term;
+      if (term < 1e-22L * sum) break;
+    }
+    const long double e = std::exp(-(long double)T);
+    long double f = e * sum;
+    F[mmax] = (double)f;
+    for (int m = mmax - 1; m >= 0; --m) {
+      f = (2.0L * T * f + e) / (2 * m + 1);
+      F[m] = (double)f;
+    }
+  } else {
+    const double e = std::exp(-T);
+    F[0] = 0.5 * std::sqrt(M_PI / T) * std::erf(std::sqrt(T));
+    for (int m = 0; m < mmax; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) / (2.0 * T);
+  }
+}
+
+}  // namespace
+
+extern "C" int pe_init() {
+  try {
+    programs();
+  } catch (...) {
+    return -1;
+  }
+  return 0;
+}
+
+// Shells s = 0..3 (l_0 >= l_1, l_2 >= l_3): centres ctr[3s..], np[s] primitives with
+// exponents and full contraction coefficients (those multiplying the raw
+// Gaussian x^l e^{-a r^2}) concatenated in shell order.  out [n0][n1][n2][n3].
+extern "C" int pe_quartet(int la, int lb, int lc, int ld, const double *ctr, const int *np,
+                          const double *exps, const double *coefs, double *out) {
+  const ProgramSet &ps = programs();
+  if (la < lb || lc < ld) return -1;
+  const ClassProg &p = ps.progs[quartet_index(la, lb, lc, ld, 0)];
+  const double *A = ctr, *B = ctr + 3, *C = ctr + 6, *D = ctr + 9;
+  int off[5] = {0};
+  for (int s = 0; s < 4; ++s) off[s + 1] = off[s] + np[s];
+  std::vector<double> acc(p.acc_total + p.hrr_size + 1, 0.0), v(p.vrr_size), cf(kNumCoef), h(3 * p.nh);
+  std::vector<double> F(p.ltot + 1);
+  for (int i = off[0]; i < off[1]; ++i)
+    for (int j = off[1]; j < off[2]; ++j)
+      for (int k = off[2]; k < off[3]; ++k)
+        for (int l = off[3]; l < off[4]; ++l) {
+          const double a = exps[i], b = exps[j], c = exps[k], d = exps[l];
+          const double zeta = a + b, eta = c + d, rho = zeta * eta / (zeta + eta);
+          double P[3], Q[3], W[3], ab2 = 0, cd2 = 0, pq2 = 0;
+          for (int x = 0; x < 3; ++x) {
+            P[x] = (a * A[x] + b * B[x]) / zeta;
+            Q[x] = (c * C[x] + d * D[x]) / eta;
+            W[x] = (zeta * P[x] + eta * Q[x]) / (zeta + eta);
+            ab2 += (A[x] - B[x]) * (A[x] - B[x]);
+            cd2 += (C[x] - D[x]) * (C[x] - D[x]);
+            pq2 += (P[x] - Q[x]) * (P[x] - Q[x]);
+          }
+          boys(p.ltot, rho * pq2, F.data());
+          const double pre = 2.0 * std::pow(M_PI, 2.5) / (zeta * eta * std::sqrt(zeta + eta)) *
+                             std::exp(-a * b / zeta * ab2 - c * d / eta * cd2) * coefs[i] * coefs[j] *
+                             coefs[k] * coefs[l];
+          v[0] = 0.0;
+          for (int m = 0; m <= p.ltot; ++m) v[1 + m] = pre * F[m];
+          for (int x = 0; x < 3; ++x) {
+            cf[kPAx + x] = P[x] - A[x];
+            cf[kQCx + x] = Q[x] - C[x];
+            cf[kWPx + x] = W[x] - P[x];
+            cf[kWQx + x] = W[x] - Q[x];
+          }
+          cf[kRhoZeta] = rho / zeta;
+          cf[kRhoEta] = rho / eta;
+          for (int n = 0; n < p.nh; ++n) {
+            h[n] = 0.5 * n / zeta;
+            h[p.nh + n] = 0.5 * n / eta;
+            h[2 * p.nh + n] = 0.5 * n / (zeta + eta);
+          }
+          for (int L = 0; L < p.nvrr_level; ++L)
+            for (int s = ps.levels[p.vrr_level0 + L]; s < ps.levels[p.vrr_level0 + L + 1]; ++s) {
+              const VrrInstr &in = ps.vrr[s];
+              double t = cf[kPAx + 3 * in.kind + in.dir] * v[in.s0] + cf[kWPx + 3 * in.kind + in.dir] * v[in.s1];
+              if (in.n1) t += h[in.kind * p.nh + in.n1] * (v[in.s2] - cf[kRhoZeta + in.kind] * v[in.s3]);
+              if (in.n2) t += h[2 * p.nh + in.n2] * v[in.s4];
+              v[in.tgt] = t;
+            }
+          for (int s = p.acc_begin; s < p.acc_begin + p.nacc; ++s) acc[ps.acc[s].acc] += v[ps.acc[s].slot];
+        }
+  const TileProg &T = ps.tiles[p.tile_begin];
+  double X[2][3];
+  for (int x = 0; x < 3; ++x) {
+    X[0][x] = A[x] - B[x];
+    X[1][x] = C[x] - D[x];
+  }
+  acc[p.acc_total] = 0.0;
+  for (int L = 0; L < T.nhrr_level; ++L)
+    for (int s = ps.levels[T.hrr_level0 + L]; s < ps.levels[T.hrr_level0 + L + 1]; ++s) {
+      const HrrInstr &in = ps.hrr[s];
+      const double c = in.kind < 2 ? X[in.kind][in.dir] : -double(in.dir);
+      acc[in.tgt] = c * acc[in.s1] + acc[in.s0];
+    }
+  for (int o = 0; o < T.nout; ++o) out[o] = acc[T.out_base + o];
+  return 0;
+}

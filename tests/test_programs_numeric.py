@@ -1,0 +1,73 @@
+"""The library's recurrence programs evaluated on the CPU (tests/program_eval.cpp
+interprets them with its own Boys function and primitive set-up) against the
+oracle's McMurchie-Davidson contracted blocks, one shell quartet of every value
+class from (ss|ss) to (dd|dd), bra and ket classes in both orders, at 1e-11
+relative to the block's largest element: the generator's vertical and
+horizontal steps, its compacted slots and its component order are right
+before any kernel runs them."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2607_05622_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+OUT = os.path.join(ROOT, "tests", "_build")
+
+
+@pytest.fixture(scope="module")
+def pe():
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    os.makedirs(OUT, exist_ok=True)
+    so = os.path.join(OUT, "libprogram_eval.so")
+    src = [os.path.join(ROOT, "tests", "program_eval.cpp"),
+           os.path.join(ROOT, "paper_2607_05622_gb300", "csrc", "program.cpp")]
+    subprocess.run([cxx, "-O2", "-std=c++17", "-shared", "-fPIC",
+                    "-I", os.path.join(ROOT, "paper_2607_05622_gb300", "csrc"),
+                    "-I", os.path.join(ROOT, "include"), *src, "-o", so], check=True)
+    lib = ctypes.CDLL(so)
+    assert lib.pe_init() == 0
+    return lib
+
+
+def _quartet(pe, oracle, mol, cn, shells):
+    ls = [int(mol.shell_l[s]) for s in shells]
+    ctr = np.concatenate([mol.coords[mol.shell_atom[s]] for s in shells]).astype(np.float64)
+    off = np.concatenate([[0], np.cumsum(mol.shell_nprim)])
+    np_ = np.array([mol.shell_nprim[s] for s in shells], dtype=np.int32)
+    ex = np.concatenate([mol.exps[off[s]:off[s + 1]] for s in shells])
+    co = np.concatenate([cn[off[s]:off[s + 1]] for s in shells])
+    n = [(l + 1) * (l + 2) // 2 for l in ls]
+    out = np.zeros(int(np.prod(n)))
+    P = ctypes.POINTER(ctypes.c_double)
+    rc = pe.pe_quartet(*ls, ctr.ctypes.data_as(P), np_.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                       ex.ctypes.data_as(P), co.ctypes.data_as(P), out.ctypes.data_as(P))
+    assert rc == 0
+    return out.reshape(n)
+
+
+def test_every_value_class_against_the_oracle(pe, oracle):
+    c, k = W.chain(2, 2)  # heavy 3s2p1d + H 2s1p, several centres
+    mol = W.build_molecule(c, k, W.draw_kind_bases(np.random.default_rng(7)))
+    cn = oracle.norm_coefs(mol)
+    by_l = {}
+    for s, l in enumerate(mol.shell_l):
+        by_l.setdefault(int(l), []).append(s)
+    rng = np.random.default_rng(1)
+    pairs = [(la, lb) for la in range(3) for lb in range(la + 1)]
+    checked = 0
+    for (la, lb) in pairs:
+        for (lc, ld) in pairs:
+            shells = [int(rng.choice(by_l[l])) for l in (la, lb, lc, ld)]
+            got = _quartet(pe, oracle, mol, cn, shells)
+            ref = oracle.shell_quartet(mol, *shells)
+            scale = np.abs(ref).max()
+            assert np.abs(got - ref).max() <= 1e-11 * scale, ((la, lb, lc, ld), np.abs(got - ref).max() / scale)
+            checked += 1
+    assert checked == 36
