@@ -5,6 +5,7 @@
 // own Boys function and primitive set-up.  The tests compare its blocks with
 // the oracle's McMurchie-Davidson blocks, which pins the program generator on
 // the CPU.  Compiled by the test itself (g++), never by the library build.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -62,11 +63,13 @@ extern "C" int pe_init() {
 // Shells s = 0..3 (l_0 >= l_1, l_2 >= l_3): centres ctr[3s..], np[s] primitives with
 // exponents and full contraction coefficients (those multiplying the raw
 // Gaussian x^l e^{-a r^2}) concatenated in shell order.  out [n0][n1][n2][n3].
-extern "C" int pe_quartet(int la, int lb, int lc, int ld, const double *ctr, const int *np,
-                          const double *exps, const double *coefs, double *out) {
+// deriv = 0: the value block [n0][n1][n2][n3]; deriv = 1: the nine derivative
+// tiles d/dA_x .. d/dC_z, each [n0][n1][n2][n3], concatenated.
+extern "C" int pe_quartet_d(int la, int lb, int lc, int ld, int deriv, const double *ctr, const int *np,
+                            const double *exps, const double *coefs, double *out) {
   const ProgramSet &ps = programs();
   if (la < lb || lc < ld) return -1;
-  const ClassProg &p = ps.progs[quartet_index(la, lb, lc, ld, 0)];
+  const ClassProg &p = ps.progs[quartet_index(la, lb, lc, ld, deriv)];
   const double *A = ctr, *B = ctr + 3, *C = ctr + 6, *D = ctr + 9;
   int off[5] = {0};
   for (int s = 0; s < 4; ++s) off[s + 1] = off[s] + np[s];
@@ -101,6 +104,9 @@ extern "C" int pe_quartet(int la, int lb, int lc, int ld, const double *ctr, con
           }
           cf[kRhoZeta] = rho / zeta;
           cf[kRhoEta] = rho / eta;
+          cf[kWA] = 2.0 * a;  // derivative channels: 2 alpha, 2 beta, 2 gamma
+          cf[kWB] = 2.0 * b;
+          cf[kWC] = 2.0 * c;
           for (int n = 0; n < p.nh; ++n) {
             h[n] = 0.5 * n / zeta;
             h[p.nh + n] = 0.5 * n / eta;
@@ -114,21 +120,33 @@ extern "C" int pe_quartet(int la, int lb, int lc, int ld, const double *ctr, con
               if (in.n2) t += h[2 * p.nh + in.n2] * v[in.s4];
               v[in.tgt] = t;
             }
-          for (int s = p.acc_begin; s < p.acc_begin + p.nacc; ++s) acc[ps.acc[s].acc] += v[ps.acc[s].slot];
+          for (int s = p.acc_begin; s < p.acc_begin + p.nacc; ++s) {
+            const AccInstr &in = ps.acc[s];
+            acc[in.acc] += (in.chan == 0 ? 1.0 : cf[kWA + in.chan - 1]) * v[in.slot];
+          }
         }
-  const TileProg &T = ps.tiles[p.tile_begin];
   double X[2][3];
   for (int x = 0; x < 3; ++x) {
     X[0][x] = A[x] - B[x];
     X[1][x] = C[x] - D[x];
   }
-  acc[p.acc_total] = 0.0;
-  for (int L = 0; L < T.nhrr_level; ++L)
-    for (int s = ps.levels[T.hrr_level0 + L]; s < ps.levels[T.hrr_level0 + L + 1]; ++s) {
-      const HrrInstr &in = ps.hrr[s];
-      const double c = in.kind < 2 ? X[in.kind][in.dir] : -double(in.dir);
-      acc[in.tgt] = c * acc[in.s1] + acc[in.s0];
-    }
-  for (int o = 0; o < T.nout; ++o) out[o] = acc[T.out_base + o];
+  const std::vector<double> acc0(acc.begin(), acc.begin() + p.acc_total);
+  for (int tile = 0; tile < p.ntile; ++tile) {
+    const TileProg &T = ps.tiles[p.tile_begin + tile];
+    std::copy(acc0.begin(), acc0.end(), acc.begin());
+    acc[p.acc_total] = 0.0;
+    for (int L = 0; L < T.nhrr_level; ++L)
+      for (int s = ps.levels[T.hrr_level0 + L]; s < ps.levels[T.hrr_level0 + L + 1]; ++s) {
+        const HrrInstr &in = ps.hrr[s];
+        const double c = in.kind < 2 ? X[in.kind][in.dir] : -double(in.dir);
+        acc[in.tgt] = c * acc[in.s1] + acc[in.s0];
+      }
+    for (int o = 0; o < T.nout; ++o) out[(size_t)tile * T.nout + o] = acc[T.out_base + o];
+  }
   return 0;
+}
+
+extern "C" int pe_quartet(int la, int lb, int lc, int ld, const double *ctr, const int *np,
+                          const double *exps, const double *coefs, double *out) {
+  return pe_quartet_d(la, lb, lc, ld, 0, ctr, np, exps, coefs, out);
 }

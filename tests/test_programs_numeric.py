@@ -2,9 +2,10 @@
 interprets them with its own Boys function and primitive set-up) against the
 oracle's McMurchie-Davidson contracted blocks, one shell quartet of every value
 class from (ss|ss) to (dd|dd), bra and ket classes in both orders, at 1e-11
-relative to the block's largest element: the generator's vertical and
-horizontal steps, its compacted slots and its component order are right
-before any kernel runs them."""
+relative to the block's largest element; and the derivative programs' nine
+tiles against central differences of the oracle's blocks: the generator's
+vertical and horizontal steps, its compacted slots, channel weights and
+component order are right before any kernel runs them."""
 import ctypes
 import os
 import shutil
@@ -71,3 +72,49 @@ def test_every_value_class_against_the_oracle(pe, oracle):
             assert np.abs(got - ref).max() <= 1e-11 * scale, ((la, lb, lc, ld), np.abs(got - ref).max() / scale)
             checked += 1
     assert checked == 36
+
+
+def test_derivative_tiles_against_finite_differences(pe, oracle):
+    """Derivative programs (four weighted channels, nine (centre, direction)
+    tiles): each tile equals the central difference of the oracle's value block
+    when only that shell's centre moves (four shells on four atoms)."""
+    c, k = W.chain(2, 2)
+    base = W.build_molecule(c, k, W.draw_kind_bases(np.random.default_rng(7)))
+    # one shell per atom: a d shell, a p shell, a p shell and an s shell
+    atoms = {}
+    for s, (a, l) in enumerate(zip(base.shell_atom, base.shell_l)):
+        atoms.setdefault(int(a), {})[int(l)] = s
+    pick = []
+    for l, a in ((2, 0), (1, 2), (1, 1), (0, 3)):
+        pick.append(atoms[a][l])
+    cn = oracle.norm_coefs(base)
+    got = _quartet_d(pe, base, cn, pick)
+    h = 1e-4
+    scale = None
+    for centre in range(3):
+        for x in range(3):
+            blocks = []
+            for sgn in (1.0, -1.0):
+                cc = base.coords.copy()
+                cc[base.shell_atom[pick[centre]], x] += sgn * h
+                blocks.append(oracle.shell_quartet(base.with_coords(cc), *pick))
+            fd = (blocks[0] - blocks[1]) / (2 * h)
+            scale = np.abs(fd).max() if scale is None else max(scale, np.abs(fd).max())
+            tile = got[3 * centre + x]
+            assert np.abs(tile - fd).max() <= 1e-6 * np.abs(fd).max() + 1e-9, (centre, x)
+
+
+def _quartet_d(pe, mol, cn, shells):
+    ls = [int(mol.shell_l[s]) for s in shells]
+    ctr = np.concatenate([mol.coords[mol.shell_atom[s]] for s in shells]).astype(np.float64)
+    off = np.concatenate([[0], np.cumsum(mol.shell_nprim)])
+    np_ = np.array([mol.shell_nprim[s] for s in shells], dtype=np.int32)
+    ex = np.concatenate([mol.exps[off[s]:off[s + 1]] for s in shells])
+    co = np.concatenate([cn[off[s]:off[s + 1]] for s in shells])
+    n = [(l + 1) * (l + 2) // 2 for l in ls]
+    out = np.zeros(9 * int(np.prod(n)))
+    P = ctypes.POINTER(ctypes.c_double)
+    rc = pe.pe_quartet_d(*ls, 1, ctr.ctypes.data_as(P), np_.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                         ex.ctypes.data_as(P), co.ctypes.data_as(P), out.ctypes.data_as(P))
+    assert rc == 0
+    return out.reshape([9] + n)
