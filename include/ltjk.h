@@ -151,21 +151,29 @@ int ltjk_schwarz(const ltjk_ctx *ctx, double *Q_host);
 
 /* ------------------------------------------------------ Laplace quadrature */
 /* Least-squares exponential sum sum_q w_q exp(-t_q x) ~ 1/x on [xmin, xmax]
-   (Eq. laplace), fitted on the relative residual by Levenberg-Marquardt with
-   continuation in the number of points.  Host-only, synchronous.
+   (Eq. laplace), fitted on the relative residual: the weights are the linear
+   least-squares solution for given exponents (variable projection) and
+   Levenberg-Marquardt moves the exponents, with continuation in the number
+   of points.  Once an added point no longer lowers the residual (the fit has
+   reached what double precision allows on the range), the remaining points
+   are placed in the widest gaps with a weight of 1e-16 of the smallest, so
+   n points are always returned.  Fits are cached per range.  Host-only,
+   synchronous, thread-safe.
      0 < xmin < xmax, 1 <= n <= 32; t_host[n], w_host[n] receive the nodes
-     (ascending) and weights; *max_rel_err (nullable) receives
-     max |x sum w exp(-t x) - 1| on 10^5 log-spaced points of [xmin, xmax]. */
+     (strictly ascending) and weights (positive); *max_rel_err (nullable)
+     receives max |x sum w exp(-t x) - 1| on 10^5 log-spaced points of
+     [xmin, xmax]. */
 int ltjk_laplace_quadrature(double xmin, double xmax, int n, double *t_host, double *w_host,
                             double *max_rel_err);
 
 /* Minimax (best uniform relative error) exponential sum for 1/x on
-   [xmin, xmax] -- the grid the paper prescribes (Eq. laplace) -- by the Remez
-   exchange started from the least-squares fit: the relative error of the
-   result equioscillates at 2n+1 points.  Host-only, synchronous.  Arguments
-   as ltjk_laplace_quadrature; *converged (nullable) is 1 when the exchange
-   levelled the error, 0 when it stopped early (the nodes returned are then
-   the least-squares ones). */
+   [xmin, xmax] -- the grid the paper prescribes (Eq. laplace): Lawson
+   reweighting of the least-squares fit, then the Remez exchange (the
+   levelled-error equations solved with the weights projected out); the
+   relative error of the result equioscillates at 2n+1 points.  Host-only,
+   synchronous.  Arguments as ltjk_laplace_quadrature; *converged (nullable)
+   is 1 when the exchange levelled the error, 0 when it did not (the nodes
+   returned are then the least-squares ones). */
 int ltjk_laplace_minimax(double xmin, double xmax, int n, double *t_host, double *w_host,
                          double *max_rel_err, int *converged);
 
