@@ -3,7 +3,7 @@ interprets them with its own Boys function and primitive set-up) against the
 oracle's McMurchie-Davidson contracted blocks, one shell quartet of every value
 class from (ss|ss) to (dd|dd), bra and ket classes in both orders, at 1e-11
 relative to the block's largest element; and the derivative programs' nine
-tiles against central differences of the oracle's blocks: the generator's
+tiles, every class, against central differences of the oracle's blocks: the generator's
 vertical and horizontal steps, its compacted slots, channel weights and
 component order are right before any kernel runs them."""
 import ctypes
@@ -118,3 +118,47 @@ def _quartet_d(pe, mol, cn, shells):
                          ex.ctypes.data_as(P), co.ctypes.data_as(P), out.ctypes.data_as(P))
     assert rc == 0
     return out.reshape([9] + n)
+
+
+def test_every_derivative_class_against_finite_differences(pe, oracle):
+    """All 36 derivative classes, (ss|ss) to (dd|dd) with bra and ket classes in
+    both orders: each of the nine (centre, direction) tiles equals the central
+    difference of the oracle's value block when only that shell's atom moves.
+    The four shells sit on four atoms placed off any plane, so no direction's
+    derivative vanishes by symmetry."""
+    rng = np.random.default_rng(11)
+    coords = [np.zeros(3)]
+    while len(coords) < 4:  # four heavy atoms 1.3 to 2.6 bohr apart, in 3D
+        p = coords[-1] + rng.normal(size=3)
+        d = min(np.linalg.norm(p - q) for q in coords)
+        if 1.3 <= d <= 2.6:
+            coords.append(p)
+    mol = W.build_molecule([tuple(c) for c in coords], ["heavy"] * 4,
+                           W.draw_kind_bases(np.random.default_rng(7)))
+    off = np.concatenate([[0], np.cumsum(mol.shell_nprim)])
+    first = {}  # the most diffuse shell of each l on each atom: blocks of order 0.1, not 1e-9
+    for s, (a, l) in enumerate(zip(mol.shell_atom, mol.shell_l)):
+        key, lo = (int(a), int(l)), mol.exps[off[s]:off[s + 1]].min()
+        if key not in first or lo < first[key][1]:
+            first[key] = (s, lo)
+    cn = oracle.norm_coefs(mol)
+    pairs = [(la, lb) for la in range(3) for lb in range(la + 1)]
+    h = 1e-4
+    checked = 0
+    for (la, lb) in pairs:
+        for (lc, ld) in pairs:
+            pick = [first[(atom, l)][0] for atom, l in enumerate((la, lb, lc, ld))]
+            got = _quartet_d(pe, mol, cn, pick)
+            for centre in range(3):
+                for x in range(3):
+                    blocks = []
+                    for sgn in (1.0, -1.0):
+                        cc = mol.coords.copy()
+                        cc[centre, x] += sgn * h
+                        blocks.append(oracle.shell_quartet(mol.with_coords(cc), *pick))
+                    fd = (blocks[0] - blocks[1]) / (2 * h)
+                    err = np.abs(got[3 * centre + x] - fd).max()
+                    assert np.abs(fd).max() > 1e-5, ((la, lb, lc, ld), centre, x)
+                    assert err <= 1e-6 * np.abs(fd).max(), ((la, lb, lc, ld), centre, x, err)
+            checked += 1
+    assert checked == 36
