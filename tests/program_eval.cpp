@@ -150,3 +150,93 @@ extern "C" int pe_quartet(int la, int lb, int lc, int ld, const double *ctr, con
                           const double *exps, const double *coefs, double *out) {
   return pe_quartet_d(la, lb, lc, ld, 0, ctr, np, exps, coefs, out);
 }
+
+// The same quartet with the recurrences in IEEE binary32, in the operation
+// order of the integral kernel's single-precision class: base values and
+// coefficients computed in binary64 and rounded once to binary32, each
+// vertical step as fused multiply-adds (PA v0, + WP v1, + n/2zeta (v2 -
+// rho/zeta v3), + n/2(zeta+eta) v4), the accumulation over primitive quartets
+// and the horizontal steps as binary32 fused multiply-adds.  Used to measure
+// the error of single-precision quartets against the oracle's blocks, from
+// which the mixed-precision tolerance is derived.
+extern "C" int pe_quartet_f32(int la, int lb, int lc, int ld, int deriv, const double *ctr, const int *np,
+                              const double *exps, const double *coefs, double *out) {
+  const ProgramSet &ps = programs();
+  if (la < lb || lc < ld) return -1;
+  const ClassProg &p = ps.progs[quartet_index(la, lb, lc, ld, deriv)];
+  const double *A = ctr, *B = ctr + 3, *C = ctr + 6, *D = ctr + 9;
+  int off[5] = {0};
+  for (int s = 0; s < 4; ++s) off[s + 1] = off[s] + np[s];
+  std::vector<float> acc(p.acc_total + p.hrr_size + 1, 0.0f), v(p.vrr_size), cf(kNumCoef), h(3 * p.nh);
+  std::vector<double> F(p.ltot + 1);
+  for (int i = off[0]; i < off[1]; ++i)
+    for (int j = off[1]; j < off[2]; ++j)
+      for (int k = off[2]; k < off[3]; ++k)
+        for (int l = off[3]; l < off[4]; ++l) {
+          const double a = exps[i], b = exps[j], c = exps[k], d = exps[l];
+          const double zeta = a + b, eta = c + d, rho = zeta * eta / (zeta + eta);
+          double P[3], Q[3], W[3], ab2 = 0, cd2 = 0, pq2 = 0;
+          for (int x = 0; x < 3; ++x) {
+            P[x] = (a * A[x] + b * B[x]) / zeta;
+            Q[x] = (c * C[x] + d * D[x]) / eta;
+            W[x] = (zeta * P[x] + eta * Q[x]) / (zeta + eta);
+            ab2 += (A[x] - B[x]) * (A[x] - B[x]);
+            cd2 += (C[x] - D[x]) * (C[x] - D[x]);
+            pq2 += (P[x] - Q[x]) * (P[x] - Q[x]);
+          }
+          boys(p.ltot, rho * pq2, F.data());
+          const double pre = 2.0 * std::pow(M_PI, 2.5) / (zeta * eta * std::sqrt(zeta + eta)) *
+                             std::exp(-a * b / zeta * ab2 - c * d / eta * cd2) * coefs[i] * coefs[j] *
+                             coefs[k] * coefs[l];
+          v[0] = 0.0f;
+          for (int m = 0; m <= p.ltot; ++m) v[1 + m] = (float)(pre * F[m]);
+          for (int x = 0; x < 3; ++x) {
+            cf[kPAx + x] = (float)(P[x] - A[x]);
+            cf[kQCx + x] = (float)(Q[x] - C[x]);
+            cf[kWPx + x] = (float)(W[x] - P[x]);
+            cf[kWQx + x] = (float)(W[x] - Q[x]);
+          }
+          cf[kRhoZeta] = (float)(rho / zeta);
+          cf[kRhoEta] = (float)(rho / eta);
+          cf[kWA] = (float)(2.0 * a);
+          cf[kWB] = (float)(2.0 * b);
+          cf[kWC] = (float)(2.0 * c);
+          for (int n = 0; n < p.nh; ++n) {
+            h[n] = (float)(0.5 * n / zeta);
+            h[p.nh + n] = (float)(0.5 * n / eta);
+            h[2 * p.nh + n] = (float)(0.5 * n / (zeta + eta));
+          }
+          for (int L = 0; L < p.nvrr_level; ++L)
+            for (int s = ps.levels[p.vrr_level0 + L]; s < ps.levels[p.vrr_level0 + L + 1]; ++s) {
+              const VrrInstr &in = ps.vrr[s];
+              float t = cf[kPAx + 3 * in.kind + in.dir] * v[in.s0];
+              t = std::fma(cf[kWPx + 3 * in.kind + in.dir], v[in.s1], t);
+              if (in.n1) t = std::fma(h[in.kind * p.nh + in.n1], std::fma(-cf[kRhoZeta + in.kind], v[in.s3], v[in.s2]), t);
+              if (in.n2) t = std::fma(h[2 * p.nh + in.n2], v[in.s4], t);
+              v[in.tgt] = t;
+            }
+          for (int s = p.acc_begin; s < p.acc_begin + p.nacc; ++s) {
+            const AccInstr &in = ps.acc[s];
+            acc[in.acc] = std::fma(in.chan == 0 ? 1.0f : cf[kWA + in.chan - 1], v[in.slot], acc[in.acc]);
+          }
+        }
+  float X[2][3];
+  for (int x = 0; x < 3; ++x) {
+    X[0][x] = (float)(A[x] - B[x]);
+    X[1][x] = (float)(C[x] - D[x]);
+  }
+  const std::vector<float> acc0(acc.begin(), acc.begin() + p.acc_total);
+  for (int tile = 0; tile < p.ntile; ++tile) {
+    const TileProg &T = ps.tiles[p.tile_begin + tile];
+    std::copy(acc0.begin(), acc0.end(), acc.begin());
+    acc[p.acc_total] = 0.0f;
+    for (int L = 0; L < T.nhrr_level; ++L)
+      for (int s = ps.levels[T.hrr_level0 + L]; s < ps.levels[T.hrr_level0 + L + 1]; ++s) {
+        const HrrInstr &in = ps.hrr[s];
+        const float c = in.kind < 2 ? X[in.kind][in.dir] : -float(in.dir);
+        acc[in.tgt] = std::fma(c, acc[in.s1], acc[in.s0]);
+      }
+    for (int o = 0; o < T.nout; ++o) out[(size_t)tile * T.nout + o] = acc[T.out_base + o];
+  }
+  return 0;
+}
