@@ -52,6 +52,7 @@ extern "C" {
 #define LTJK_ENOTREADY (-8)     /* result not yet available */
 
 #define LTJK_MAX_L 2            /* largest shell angular momentum of the value build */
+#define LTJK_MAX_PRIM 8         /* largest number of primitives in one shell */
 
 #define LTJK_FP64 0         /* FP64-class: double-float recurrences and digestion */
 #define LTJK_MIXED 1        /* FP32 below the Schwarz threshold, FP64-class above */
@@ -136,7 +137,12 @@ typedef struct {
    primitive-pair data, evaluates the Schwarz factors on the device, sorts the
    pairs by class and Q and builds the screened quartet work lists (Schwarz
    screening, cf. the paper's Sect. "Cost" and its screening discussion).
-   Synchronous.  *out receives the context. */
+   Synchronous.  *out receives the context (null on any error).  The basis and
+   options are checked on the host before the first CUDA call: l above
+   LTJK_MAX_L gives LTJK_EUNSUPPORTED; a negative l, a primitive count outside
+   1..LTJK_MAX_PRIM, an atom index out of range, a non-positive or non-finite
+   exponent, a non-finite coordinate, an unknown precision or a negative or
+   NaN threshold give LTJK_EINVAL. */
 int ltjk_context_create(const ltjk_basis *basis, const ltjk_opts *opts, ltjk_ctx **out);
 /* Release a context.  Work that uses it must have completed: synchronise the
    streams it was used on (or wait for its service requests) first.  Device

@@ -610,6 +610,8 @@ int ltjk_launch_count(unsigned long long *count) {
 }
 int ltjk_version(void) { return 100; }
 
+static_assert(kMaxPrim == LTJK_MAX_PRIM, "primitive limit of the header and the kernels");
+
 int ltjk_context_create(const ltjk_basis *bs, const ltjk_opts *opts, ltjk_ctx **out) {
   if (!bs || !opts || !out) return set_error(LTJK_EINVAL, "context_create: null argument");
   *out = nullptr;
@@ -625,7 +627,6 @@ int ltjk_context_create(const ltjk_basis *bs, const ltjk_opts *opts, ltjk_ctx **
   auto c = std::make_unique<ltjk_ctx>();
   c->opts = *opts;
   c->device = opts->device;
-  CUDA_TRY(cudaSetDevice(c->device));
   c->natoms = bs->natoms;
   c->nshells = bs->nshells;
   c->coords.assign(bs->coords_host, bs->coords_host + 3 * bs->natoms);
@@ -654,6 +655,8 @@ int ltjk_context_create(const ltjk_basis *bs, const ltjk_opts *opts, ltjk_ctx **
   for (int s = 0; s < c->nshells; ++s)
     normalise_shell(c->sh_l[s], c->sh_nprim[s], &c->exps[c->sh_p0[s]], bs->coefs_host + c->sh_p0[s],
                     &c->ncoef[c->sh_p0[s]]);
+  // the basis is checked on the host before the first CUDA call
+  CUDA_TRY(cudaSetDevice(c->device));
   int rc;
   if ((rc = device_programs(c->device, &c->progs, &c->boys))) return rc;
   CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));

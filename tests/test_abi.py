@@ -128,3 +128,89 @@ def test_library_minimax_equioscillates_on_the_chain_range(L, oracle):
     peaks = np.array([r.max() for r in runs])
     assert len(peaks) == 17
     assert peaks.max() <= peaks.min() * (1 + 1e-3)
+
+
+def _zero_args(argtypes):
+    out = []
+    for a in argtypes:
+        if a is ctypes.c_double:
+            out.append(0.0)
+        elif a is ctypes.c_void_p:
+            out.append(None)
+        else:
+            out.append(0)
+    return out
+
+
+def test_null_handles_are_rejected_before_any_device_work(L):
+    """Every entry point that takes a context or a service returns LTJK_EINVAL
+    for a null handle (zero sizes, null buffers), with a message naming the
+    call, and touches no device: this runs without a GPU."""
+    lib = L.lib()
+    skip = {"ltjk_last_error", "ltjk_version", "ltjk_context_create", "ltjk_service_create",
+            "ltjk_laplace_quadrature", "ltjk_laplace_minimax", "ltjk_laplace_shift",
+            "ltjk_class_program", "ltjk_launch_count"}
+    checked = 0
+    for name, (args, _) in L.SIGNATURES.items():
+        if name in skip:
+            continue
+        assert args and args[0] is ctypes.c_void_p, name
+        rc = getattr(lib, name)(*_zero_args(args))
+        assert rc == L.EINVAL, (name, rc)
+        msg = lib.ltjk_last_error().decode()
+        assert name[len("ltjk_"):] in msg, (name, msg)
+        checked += 1
+    assert checked >= 20
+    assert lib.ltjk_launch_count(None) == L.EINVAL
+    assert lib.ltjk_class_program(0, 0, 0, 0, 0, None) == L.EINVAL
+    assert lib.ltjk_laplace_shift(0, None, None, 0.0, None) == L.EINVAL
+
+
+def test_last_error_is_per_thread(L):
+    import threading
+    lib = L.lib()
+    assert lib.ltjk_nao(None, None) == L.EINVAL
+    seen = {}
+
+    def other():
+        seen["before"] = lib.ltjk_last_error().decode()
+        lib.ltjk_jk_grad(None, 0, None, None, 0.0, 0.0, None, None)
+        seen["after"] = lib.ltjk_last_error().decode()
+
+    th = threading.Thread(target=other)
+    th.start()
+    th.join()
+    assert "nao" not in seen["before"] and "jk_grad" in seen["after"]
+    assert "nao" in lib.ltjk_last_error().decode()
+
+
+def _basis(L, l, nprim=1, atom=0, exps=1.0):
+    keep = [np.zeros((1, 3)), np.array([atom], dtype=np.int32), np.array([l], dtype=np.int32),
+            np.array([nprim], dtype=np.int32), np.full(max(nprim, 1), exps), np.ones(max(nprim, 1))]
+    c, a, ll, n, e, k = keep
+    b = L._Basis(1, c.ctypes.data, 1, a.ctypes.data, ll.ctypes.data, n.ctypes.data, e.ctypes.data,
+                 k.ctypes.data)
+    return b, keep
+
+
+def test_context_create_checks_the_basis_on_the_host(L):
+    """A basis the library cannot take is refused before the first CUDA call:
+    l above LTJK_MAX_L (f shells) is LTJK_EUNSUPPORTED, a bad primitive count,
+    atom index, exponent, precision or threshold LTJK_EINVAL."""
+    lib = L.lib()
+    h = ctypes.c_void_p()
+    o = L._Opts(1e-12, 1e-6, L.FP64, 0)
+    cases = [(dict(l=L.MAX_L + 1), L.EUNSUPPORTED, "above LTJK_MAX_L"),
+             (dict(l=-1), L.EINVAL, "negative"),
+             (dict(l=0, nprim=0), L.EINVAL, "nprim"),
+             (dict(l=0, atom=1), L.EINVAL, "atom"),
+             (dict(l=0, exps=-1.0), L.EINVAL, "exponent")]
+    for kw, code, text in cases:
+        b, keep = _basis(L, **kw)
+        assert lib.ltjk_context_create(ctypes.byref(b), ctypes.byref(o), ctypes.byref(h)) == code, kw
+        assert text in lib.ltjk_last_error().decode(), (kw, lib.ltjk_last_error())
+        assert not h.value
+    b, keep = _basis(L, 0)
+    for bad in (L._Opts(1e-12, 1e-6, 7, 0), L._Opts(-1.0, 1e-6, L.FP64, 0),
+                L._Opts(1e-12, float("nan"), L.FP64, 0)):
+        assert lib.ltjk_context_create(ctypes.byref(b), ctypes.byref(bad), ctypes.byref(h)) == L.EINVAL
