@@ -8,10 +8,13 @@ Contents (each function cites the passage it follows):
   * ctypes wrappers around ``oracle.c`` (McMurchie-Davidson ERIs, J/K, gradient);
   * J/K and the energy functional written as literal sums over a full AO
     tensor (Eq. jkbuild, Eq. jkderiv);
-  * the least-squares Laplace quadrature (Eq. laplace), step by step;
+  * the least-squares Laplace quadrature (Eq. laplace), step by step, the
+    minimax grid by the Remez exchange and the omega-shifted weights
+    (Eq. eomshift);
   * Laplace pseudo-densities (Eqs. scaledcoeff, aodens/aodensk with R = X);
   * the brute-force energy-denominator sums that the quadrature must reproduce
     (Eq. factorize);
+  * the Laplace-Fock back-transform to the MO basis (Eq. laplacefock);
   * the Cholesky-factorised two-electron operator and J/K read off it
     (Eqs. cdfact, cdj, cdknonsym), step by step;
   * the Cartesian -> real-spherical transformation of AO matrices.
