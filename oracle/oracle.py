@@ -435,7 +435,8 @@ def sph_block(l: int) -> np.ndarray:
     Cartesian components (descending l_x, then l_y; every component carries the
     normalisation of x^l).  s: 1; p: x, y, z kept in Cartesian order; d, in the
     order m = -2..2: sqrt3 xy, sqrt3 yz, (2 zz - xx - yy)/2, sqrt3 xz,
-    sqrt3/2 (xx - yy)."""
+    sqrt3/2 (xx - yy); f, m = -3..3, from the degree-3 solid harmonics below
+    (the library has no f shells yet: this is the oracle for that row)."""
     if l == 0:
         return np.ones((1, 1))
     if l == 1:
@@ -448,7 +449,44 @@ def sph_block(l: int) -> np.ndarray:
                          [-0.5, 0.0, 0.0, -0.5, 0.0, 1.0],
                          [0.0, 0.0, r3, 0.0, 0.0, 0.0],
                          [r3 / 2, 0.0, 0.0, -r3 / 2, 0.0, 0.0]])
-    raise ValueError("spherical transform defined for l <= 2")
+    if l == 3:
+        return _sph_from_polynomials(3, _F_HARMONICS)
+    raise ValueError("spherical transform defined for l <= 3")
+
+
+# Real solid harmonics of degree 3, m = -3..3, as integer polynomials
+# {(lx, ly, lz): coefficient}: y(3x^2 - y^2), xyz, y(4z^2 - x^2 - y^2),
+# z(2z^2 - 3x^2 - 3y^2), x(4z^2 - x^2 - y^2), z(x^2 - y^2), x(x^2 - 3y^2).
+_F_HARMONICS = [
+    {(2, 1, 0): 3, (0, 3, 0): -1},
+    {(1, 1, 1): 1},
+    {(0, 1, 2): 4, (2, 1, 0): -1, (0, 3, 0): -1},
+    {(0, 0, 3): 2, (2, 0, 1): -3, (0, 2, 1): -3},
+    {(1, 0, 2): 4, (3, 0, 0): -1, (1, 2, 0): -1},
+    {(2, 0, 1): 1, (0, 2, 1): -1},
+    {(3, 0, 0): 1, (1, 2, 0): -3},
+]
+
+
+def _sph_from_polynomials(l: int, polys) -> np.ndarray:
+    """Rows of T for polynomials given on the monomials: every Cartesian
+    component carries the normalisation of x^l, so their one-centre overlap is
+    (lx+lx'-1)!! (ly+ly'-1)!! (lz+lz'-1)!! / (2l-1)!! (zero for an odd sum);
+    each row is scaled to unit norm under that overlap."""
+    comps = [(lx, ly, l - lx - ly) for lx in range(l, -1, -1) for ly in range(l - lx, -1, -1)]
+
+    def dfact(n):  # (n)!! with (-1)!! = 1
+        return 1.0 if n <= 0 else n * dfact(n - 2)
+
+    def ov(a, b):
+        e = [a[k] + b[k] for k in range(3)]
+        if any(v % 2 for v in e):
+            return 0.0
+        return dfact(e[0] - 1) * dfact(e[1] - 1) * dfact(e[2] - 1) / dfact(2 * l - 1)
+
+    G = np.array([[ov(a, b) for b in comps] for a in comps])
+    T = np.array([[float(p.get(c, 0)) for c in comps] for p in polys])
+    return T / np.sqrt(np.einsum("ij,jk,ik->i", T, G, T))[:, None]
 
 
 def sph_transform(mol) -> np.ndarray:
