@@ -198,7 +198,8 @@ int ltjk_laplace_shift(int n, const double *t_host, const double *w_host, double
    applied.
      C_occ [N][nocc], C_vir [N][nvir], eps_occ [nocc], eps_vir [nvir] (device),
      X [npair][nocc][nvir] (device), t_host [nlap] (host),
-     D [nlap*npair][N][N] (device, overwritten). */
+     D [nlap*npair][N][N] (device, overwritten).  nocc, nvir, npair, nlap >= 1
+     and npair * nlap <= 4096, else LTJK_EINVAL. */
 int ltjk_pseudo_densities(ltjk_ctx *ctx, int nocc, int nvir, const double *C_occ,
                           const double *C_vir, const double *eps_occ, const double *eps_vir,
                           int npair, const double *X, int nlap, const double *t_host, double *D,
