@@ -163,8 +163,11 @@ int ltjk_schwarz(const ltjk_ctx *ctx, double *Q_host);
    of points.  Once an added point no longer lowers the residual (the fit has
    reached what double precision allows on the range), the remaining points
    are placed in the widest gaps with a weight of 1e-16 of the smallest, so
-   n points are always returned.  Fits are cached per range.  Host-only,
-   synchronous, thread-safe.
+   n points are always returned.  The fit is made on [1, R_g] in units of
+   xmin, log R_g = log(xmax / xmin) rounded up to a multiple of 1/8, so the
+   nodes depend only on n and that cell (never on earlier calls); the steps
+   of each continuation are cached per cell.  Host-only, synchronous,
+   thread-safe.
      0 < xmin < xmax, 1 <= n <= 32; t_host[n], w_host[n] receive the nodes
      (strictly ascending) and weights (positive); *max_rel_err (nullable)
      receives max |x sum w exp(-t x) - 1| on 10^5 log-spaced points of

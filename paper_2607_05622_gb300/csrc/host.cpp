@@ -315,14 +315,23 @@ bool all_positive(const std::vector<double> &w) {
 }
 
 // Continuation in the number of points up to n; th/w receive the active
-// nodes (log t, ascending) and their weights.
-void fit_continuation(const LapFit &F, double R, int n, std::vector<double> &th, std::vector<double> &w) {
-  th = {std::log(1.0 / std::sqrt(R))};
+// nodes (log t, ascending) and their weights.  A non-empty th on entry is an
+// earlier step of this same continuation (same F, fewer nodes, ascending),
+// which it resumes from unchanged, so the result does not depend on whether
+// the earlier steps were cached.  path, when given, receives the active nodes
+// after every accepted step, keyed by their number.
+void fit_continuation(const LapFit &F, double R, int n, std::vector<double> &th, std::vector<double> &w,
+                      std::map<int, std::vector<double>> *path) {
   auto proj = [&F](const std::vector<double> &x, std::vector<double> *ww, std::vector<double> *rr) {
     return F.project(x, ww, rr);
   };
-  double cost = varpro_lm(proj, th, w, 300);
-  for (int k = 2; k <= n; ++k) {
+  double cost = th.empty() ? 1e300 : F.project(th, &w, nullptr);
+  if (cost >= 1e300) {
+    th = {std::log(1.0 / std::sqrt(R))};
+    cost = varpro_lm(proj, th, w, 300);
+  }
+  if (path) (*path)[(int)th.size()] = th;
+  while ((int)th.size() < n) {
     const int km = (int)th.size();
     const double step = km > 1 ? th[km - 1] - th[km - 2] : std::log(3.0);
     const double step0 = km > 1 ? th[1] - th[0] : std::log(3.0);
@@ -355,6 +364,7 @@ void fit_continuation(const LapFit &F, double R, int n, std::vector<double> &th,
     w = bw;
     sort_pairs(th, w);
     cost = best;
+    if (path) (*path)[(int)th.size()] = th;
   }
 }
 
@@ -398,54 +408,44 @@ int laplace_quadrature(double xmin, double xmax, int n, double *t_out, double *w
                        double *err_out) {
   if (!(xmin > 0) || !(xmax > xmin) || !std::isfinite(xmax) || n < 1 || n > 32 || !t_out || !w_out)
     return set_error(LTJK_EINVAL, "laplace_quadrature: need 0 < xmin < xmax and 1 <= n <= 32");
-  // Cache of normalised active nodes per n, keyed by log R: an exact hit is
-  // reused, a nearby one warm-starts the refinement.
+  // The fit is made on [1, Rg] with log Rg = log R rounded up to a multiple of
+  // 1/8 (Rg / R < 1.14; a fit on the wider range is valid on the requested
+  // one), so the nodes depend only on n and that cell, not on the order of
+  // earlier requests.  Every step of a continuation is cached under its cell
+  // and its number of points: a request resumes the continuation from the
+  // largest cached step at or below n, which gives what a fresh continuation
+  // would.
   static std::mutex mu;
-  static std::map<int, std::map<double, std::vector<double>>> cache;
-  const double R = xmax / xmin, lR = std::log(R);
+  static std::map<std::pair<long, int>, std::vector<double>> cache;
+  const double R = xmax / xmin;
+  const long cell = std::max(1L, (long)std::ceil(8.0 * std::log(R) - 1e-12));
+  const double lRg = cell / 8.0, Rg = std::exp(lRg);
   std::vector<double> th, w;
-  bool exact = false;
+  bool hit = false;
   {
     std::lock_guard<std::mutex> g(mu);
-    auto &m = cache[n];
-    auto it = m.lower_bound(lR);
-    const std::vector<double> *near = nullptr;
-    double dist = 1e300;
-    if (it != m.end()) {
-      dist = it->first - lR;
-      near = &it->second;
-      if (dist == 0.0) exact = true;
+    for (int k = n; k >= 1 && !hit && th.empty(); --k) {
+      auto it = cache.find({cell, k});
+      if (it == cache.end()) continue;
+      th = it->second;
+      hit = k == n;
     }
-    if (!exact && it != m.begin()) {
-      auto jt = std::prev(it);
-      if (lR - jt->first < dist) {
-        dist = lR - jt->first;
-        near = &jt->second;
-      }
-    }
-    if (near && (exact || dist < 0.5)) th = *near;
   }
   LapFit F;
   const int m = 500;
-  for (int s = 0; s < m; ++s) F.xs.push_back(std::exp(lR * s / (m - 1)));
-  F.lt_lo = std::log(1e-6 / R);
+  for (int s = 0; s < m; ++s) F.xs.push_back(std::exp(lRg * s / (m - 1)));
+  F.lt_lo = std::log(1e-6 / Rg);
   F.lt_hi = std::log(1e3);
-  if (exact) {
+  if (hit) {
     F.project(th, &w, nullptr);
   } else {
-    bool warm = false;
-    if (!th.empty()) {
-      std::sort(th.begin(), th.end());
-      auto proj = [&F](const std::vector<double> &x, std::vector<double> *ww, std::vector<double> *rr) {
-        return F.project(x, ww, rr);
-      };
-      const double c = varpro_lm(proj, th, w, 300);
-      warm = c < 1e300 && all_positive(w);
-      if (warm) sort_pairs(th, w);
-    }
-    if (!warm) fit_continuation(F, R, n, th, w);
+    std::map<int, std::vector<double>> path;
+    fit_continuation(F, Rg, n, th, w, &path);
     std::lock_guard<std::mutex> g(mu);
-    cache[n][lR] = th;
+    for (const auto &kv : path) cache.emplace(std::make_pair(cell, kv.first), kv.second);
+    // a continuation that stopped below n has converged in the number of
+    // points: its fit is also the answer for every count up to n
+    for (int k = (int)th.size() + 1; k <= n; ++k) cache.emplace(std::make_pair(cell, k), th);
   }
   std::vector<double> lt = th, lw = w;
   fill_nodes(lt, lw, n);

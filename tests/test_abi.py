@@ -214,3 +214,37 @@ def test_context_create_checks_the_basis_on_the_host(L):
     for bad in (L._Opts(1e-12, 1e-6, 7, 0), L._Opts(-1.0, 1e-6, L.FP64, 0),
                 L._Opts(1e-12, float("nan"), L.FP64, 0)):
         assert lib.ltjk_context_create(ctypes.byref(b), ctypes.byref(bad), ctypes.byref(h)) == L.EINVAL
+
+
+_QUAD_SCRIPT = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+from paper_2607_05622_gb300 import ltjk as L
+out = []
+for xmin, xmax, n in {calls!r}:
+    t, w, e = L.laplace_quadrature(xmin, xmax, n)
+    out.append([t.tolist(), w.tolist(), e])
+print(json.dumps(out))
+"""
+
+
+def _quad_calls(calls):
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-c", _QUAD_SCRIPT.format(root=ROOT, calls=calls)],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def test_quadrature_does_not_depend_on_earlier_requests(L):
+    """The nodes are a function of (n, the 1/8-wide cell of log(xmax/xmin)) and
+    the range: the same request gives bit-identical nodes in a fresh process,
+    after a larger request in the same cell (whose continuation it reuses) and
+    after requests in other cells."""
+    req = (0.9, 9.2, 10)  # log R = 2.327, cell 19
+    alone = _quad_calls([req])[0]
+    after = _quad_calls([(0.85, 9.3, 16), (1.0, 3.0, 12), (0.8, 30.0, 10), req])[3]
+    assert alone[0] == after[0] and alone[1] == after[1]
+    assert alone[2] == after[2] and alone[2] < 1e-8
