@@ -190,10 +190,21 @@ struct LapFit {
     const int m = (int)xs.size(), n = (int)th.size();
     for (double v : th)
       if (!(v > lt_lo && v < lt_hi)) return 1e300;
-    std::vector<double> A((size_t)m * n), b(m, 1.0), R;
+    std::vector<double> A((size_t)m * n), b(m, 1.0), R, cn(n, 0.0);
     for (int s = 0; s < m; ++s)
       for (int q = 0; q < n; ++q) A[(size_t)s * n + q] = xs[s] * std::exp(-std::exp(th[q]) * xs[s]);
     const std::vector<double> A0 = A;
+    // columns scaled to unit norm before the factorisation: the rank test then
+    // sees the angles between the basis functions, not their sizes (a large t
+    // gives a column of tiny norm that is still well determined)
+    for (int s = 0; s < m; ++s)
+      for (int q = 0; q < n; ++q) cn[q] += A[(size_t)s * n + q] * A[(size_t)s * n + q];
+    for (int q = 0; q < n; ++q) {
+      if (!(cn[q] > 0.0)) return 1e300;
+      cn[q] = std::sqrt(cn[q]);
+    }
+    for (int s = 0; s < m; ++s)
+      for (int q = 0; q < n; ++q) A[(size_t)s * n + q] /= cn[q];
     householder_qr(m, n, A, b, R);
     double dmax = 0.0, dmin = 1e300;
     for (int q = 0; q < n; ++q) {
@@ -208,6 +219,7 @@ struct LapFit {
       for (int j = i + 1; j < n; ++j) v -= R[(size_t)i * n + j] * ww[j];
       ww[i] = v / R[(size_t)i * n + i];
     }
+    for (int q = 0; q < n; ++q) ww[q] /= cn[q];
     double c = 0.0;
     std::vector<double> rr(m);
     for (int s = 0; s < m; ++s) {

@@ -248,3 +248,13 @@ def test_quadrature_does_not_depend_on_earlier_requests(L):
     after = _quad_calls([(0.85, 9.3, 16), (1.0, 3.0, 12), (0.8, 30.0, 10), req])[3]
     assert alone[0] == after[0] and alone[1] == after[1]
     assert alone[2] == after[2] and alone[2] < 1e-8
+
+
+def test_quadrature_reaches_below_1e_9_on_narrow_ranges(L):
+    """The projection scales its basis columns before the rank test, so nodes
+    with large t are not mistaken for rank loss: on narrow ranges the
+    continuation goes on to ~1e-10 (the unscaled test stopped it at 6e-9)."""
+    for R, n, bound in ((2.0, 6, 5e-10), (5.0, 10, 2e-10), (7.0, 12, 2e-10), (10.25, 16, 2e-10)):
+        t, w, e = L.laplace_quadrature(1.0, R, n)
+        assert e < bound, (R, n, e)
+        assert np.all(np.diff(t) > 0) and np.all(w > 0)
