@@ -110,5 +110,8 @@ inline int quartet_index(int la, int lb, int lc, int ld, int deriv) {
 
 void build_programs(ProgramSet &ps);
 void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv, ClassProg &out);
+// Straight-line C++/CUDA source of one class program (codegen.cpp).
+std::string emit_class_source(const ProgramSet &ps, int la, int lb, int lc, int ld, int deriv,
+                              const std::string &prefix);
 
 }  // namespace ltjk

@@ -60,6 +60,52 @@ extern "C" int pe_init() {
   return 0;
 }
 
+namespace {
+
+// Base values [00|00]^(m) (base[m], m = 0..ltot), the CoefSlot coefficients
+// and the n/(2 zeta), n/(2 eta), n/(2 (zeta+eta)) tables of the primitive
+// quartet (a, b | c, d) with full contraction coefficients ca..cd.
+void setup_primitive(const ClassProg &p, const double *A, const double *B, const double *C, const double *D,
+                     double a, double b, double c, double d, double coef, double *base, double *cf,
+                     double *h) {
+  const double zeta = a + b, eta = c + d, rho = zeta * eta / (zeta + eta);
+  double P[3], Q[3], W[3], ab2 = 0, cd2 = 0, pq2 = 0;
+  for (int x = 0; x < 3; ++x) {
+    P[x] = (a * A[x] + b * B[x]) / zeta;
+    Q[x] = (c * C[x] + d * D[x]) / eta;
+    W[x] = (zeta * P[x] + eta * Q[x]) / (zeta + eta);
+    ab2 += (A[x] - B[x]) * (A[x] - B[x]);
+    cd2 += (C[x] - D[x]) * (C[x] - D[x]);
+    pq2 += (P[x] - Q[x]) * (P[x] - Q[x]);
+  }
+  std::vector<double> F(p.ltot + 1);
+  boys(p.ltot, rho * pq2, F.data());
+  const double pre = 2.0 * std::pow(M_PI, 2.5) / (zeta * eta * std::sqrt(zeta + eta)) *
+                     std::exp(-a * b / zeta * ab2 - c * d / eta * cd2) * coef;
+  for (int m = 0; m <= p.ltot; ++m) base[m] = pre * F[m];
+  for (int x = 0; x < 3; ++x) {
+    cf[kPAx + x] = P[x] - A[x];
+    cf[kQCx + x] = Q[x] - C[x];
+    cf[kWPx + x] = W[x] - P[x];
+    cf[kWQx + x] = W[x] - Q[x];
+  }
+  cf[kHalfZeta] = 0.5 / zeta;
+  cf[kHalfEta] = 0.5 / eta;
+  cf[kRhoZeta] = rho / zeta;
+  cf[kRhoEta] = rho / eta;
+  cf[kHalfSum] = 0.5 / (zeta + eta);
+  cf[kWA] = 2.0 * a;  // derivative channels: 2 alpha, 2 beta, 2 gamma
+  cf[kWB] = 2.0 * b;
+  cf[kWC] = 2.0 * c;
+  for (int n = 0; n < p.nh; ++n) {
+    h[n] = 0.5 * n / zeta;
+    h[p.nh + n] = 0.5 * n / eta;
+    h[2 * p.nh + n] = 0.5 * n / (zeta + eta);
+  }
+}
+
+}  // namespace
+
 // Shells s = 0..3 (l_0 >= l_1, l_2 >= l_3): centres ctr[3s..], np[s] primitives with
 // exponents and full contraction coefficients (those multiplying the raw
 // Gaussian x^l e^{-a r^2}) concatenated in shell order.  out [n0][n1][n2][n3].
@@ -74,44 +120,13 @@ extern "C" int pe_quartet_d(int la, int lb, int lc, int ld, int deriv, const dou
   int off[5] = {0};
   for (int s = 0; s < 4; ++s) off[s + 1] = off[s] + np[s];
   std::vector<double> acc(p.acc_total + p.hrr_size + 1, 0.0), v(p.vrr_size), cf(kNumCoef), h(3 * p.nh);
-  std::vector<double> F(p.ltot + 1);
   for (int i = off[0]; i < off[1]; ++i)
     for (int j = off[1]; j < off[2]; ++j)
       for (int k = off[2]; k < off[3]; ++k)
         for (int l = off[3]; l < off[4]; ++l) {
-          const double a = exps[i], b = exps[j], c = exps[k], d = exps[l];
-          const double zeta = a + b, eta = c + d, rho = zeta * eta / (zeta + eta);
-          double P[3], Q[3], W[3], ab2 = 0, cd2 = 0, pq2 = 0;
-          for (int x = 0; x < 3; ++x) {
-            P[x] = (a * A[x] + b * B[x]) / zeta;
-            Q[x] = (c * C[x] + d * D[x]) / eta;
-            W[x] = (zeta * P[x] + eta * Q[x]) / (zeta + eta);
-            ab2 += (A[x] - B[x]) * (A[x] - B[x]);
-            cd2 += (C[x] - D[x]) * (C[x] - D[x]);
-            pq2 += (P[x] - Q[x]) * (P[x] - Q[x]);
-          }
-          boys(p.ltot, rho * pq2, F.data());
-          const double pre = 2.0 * std::pow(M_PI, 2.5) / (zeta * eta * std::sqrt(zeta + eta)) *
-                             std::exp(-a * b / zeta * ab2 - c * d / eta * cd2) * coefs[i] * coefs[j] *
-                             coefs[k] * coefs[l];
           v[0] = 0.0;
-          for (int m = 0; m <= p.ltot; ++m) v[1 + m] = pre * F[m];
-          for (int x = 0; x < 3; ++x) {
-            cf[kPAx + x] = P[x] - A[x];
-            cf[kQCx + x] = Q[x] - C[x];
-            cf[kWPx + x] = W[x] - P[x];
-            cf[kWQx + x] = W[x] - Q[x];
-          }
-          cf[kRhoZeta] = rho / zeta;
-          cf[kRhoEta] = rho / eta;
-          cf[kWA] = 2.0 * a;  // derivative channels: 2 alpha, 2 beta, 2 gamma
-          cf[kWB] = 2.0 * b;
-          cf[kWC] = 2.0 * c;
-          for (int n = 0; n < p.nh; ++n) {
-            h[n] = 0.5 * n / zeta;
-            h[p.nh + n] = 0.5 * n / eta;
-            h[2 * p.nh + n] = 0.5 * n / (zeta + eta);
-          }
+          setup_primitive(p, A, B, C, D, exps[i], exps[j], exps[k], exps[l],
+                          coefs[i] * coefs[j] * coefs[k] * coefs[l], v.data() + 1, cf.data(), h.data());
           for (int L = 0; L < p.nvrr_level; ++L)
             for (int s = ps.levels[p.vrr_level0 + L]; s < ps.levels[p.vrr_level0 + L + 1]; ++s) {
               const VrrInstr &in = ps.vrr[s];
@@ -145,6 +160,41 @@ extern "C" int pe_quartet_d(int la, int lb, int lc, int ld, int deriv, const dou
   }
   return 0;
 }
+
+#ifdef LTJK_GEN_HEADER
+// The same quartet through the straight-line source the generator emits for
+// the class (tests/codegen_emit.cpp writes LTJK_GEN_HEADER): one call of the
+// class's _vrr per primitive quartet, one of its _hrr on the accumulators.
+#include LTJK_GEN_HEADER
+extern "C" int pe_quartet_gen(int la, int lb, int lc, int ld, const double *ctr, const int *np,
+                              const double *exps, const double *coefs, double *out) {
+  const GenClass *g = nullptr;
+  for (const GenClass &c : kGenClasses)
+    if (c.la == la && c.lb == lb && c.lc == lc && c.ld == ld) g = &c;
+  if (!g) return -1;
+  const ProgramSet &ps = programs();
+  const ClassProg &p = ps.progs[quartet_index(la, lb, lc, ld, LTJK_GEN_DERIV)];
+  const double *A = ctr, *B = ctr + 3, *C = ctr + 6, *D = ctr + 9;
+  int off[5] = {0};
+  for (int s = 0; s < 4; ++s) off[s + 1] = off[s] + np[s];
+  std::vector<double> acc(p.acc_total, 0.0), base(p.ltot + 1), cf(kNumCoef), h(3 * p.nh);
+  for (int i = off[0]; i < off[1]; ++i)
+    for (int j = off[1]; j < off[2]; ++j)
+      for (int k = off[2]; k < off[3]; ++k)
+        for (int l = off[3]; l < off[4]; ++l) {
+          setup_primitive(p, A, B, C, D, exps[i], exps[j], exps[k], exps[l],
+                          coefs[i] * coefs[j] * coefs[k] * coefs[l], base.data(), cf.data(), h.data());
+          g->vrr(base.data(), cf.data(), h.data(), acc.data());
+        }
+  double X[6];
+  for (int x = 0; x < 3; ++x) {
+    X[x] = A[x] - B[x];
+    X[3 + x] = C[x] - D[x];
+  }
+  g->hrr(acc.data(), X, out);
+  return 0;
+}
+#endif
 
 extern "C" int pe_quartet(int la, int lb, int lc, int ld, const double *ctr, const int *np,
                           const double *exps, const double *coefs, double *out) {
