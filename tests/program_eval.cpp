@@ -4,7 +4,10 @@
 // accumulation, the horizontal steps and the output block), with this file's
 // own Boys function and primitive set-up.  The tests compare its blocks with
 // the oracle's McMurchie-Davidson blocks, which pins the program generator on
-// the CPU.  Compiled by the test itself (g++), never by the library build.
+// the CPU.  pe_quartet_f32 runs the same programs in binary32 (the mixed
+// mode's error model); pe_quartet_gen, compiled with LTJK_GEN_HEADER, runs
+// the straight-line source the class generator emits.  Compiled by the tests
+// themselves (g++), never by the library build.
 #include <algorithm>
 #include <cmath>
 #include <vector>
