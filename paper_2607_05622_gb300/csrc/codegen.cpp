@@ -25,6 +25,8 @@
 #include <sstream>
 #include <stdexcept>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "ltjk_internal.h"
 
