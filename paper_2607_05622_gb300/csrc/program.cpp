@@ -28,11 +28,6 @@ namespace {
 using Mono = std::array<int, 3>;
 
 int mono_l(const Mono &m) { return m[0] + m[1] + m[2]; }
-// Component index within a shell (descending lx, then descending ly).
-int mono_index(const Mono &m) {
-  int l = mono_l(m);
-  return (l - m[0]) * (l - m[0] + 1) / 2 + m[2];
-}
 std::vector<Mono> monos(int l) {
   std::vector<Mono> v;
   for (int lx = l; lx >= 0; --lx)
