@@ -18,6 +18,9 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libltjk.so")
 SOURCES = ["context.cu", "host.cpp", "program.cpp"]
+# host generator of the class-specialised integral code (run before nvcc)
+GEN_SOURCES = ["gen_main.cpp", "program.cpp", "codegen.cpp"]
+GEN_INC = os.path.join(OUT, "gen_classes.inc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,12 +37,38 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
+def cxx() -> str:
+    for c in ("g++", "c++", "clang++"):
+        p = shutil.which(c)
+        if p:
+            return p
+    raise RuntimeError("no host C++ compiler found")
+
+
+def generate() -> str:
+    """Compile and run the class-code generator: writes _build/gen_classes.inc."""
+    os.makedirs(OUT, exist_ok=True)
+    exe = os.path.join(OUT, "gen_main")
+    cmd = [cxx(), "-O1", "-std=c++17", "-I", SRC, "-I", os.path.join(ROOT, "include"),
+           *[os.path.join(SRC, f) for f in GEN_SOURCES], "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"generator build failed:\n{r.stdout}\n{r.stderr}")
+    tmp = GEN_INC + f".tmp{os.getpid()}"
+    r = subprocess.run([exe, tmp], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"generator failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, GEN_INC)
+    return GEN_INC
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
         return LIB
+    generate()
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "-I", os.path.join(ROOT, "include")]
+              "-I", os.path.join(ROOT, "include"), "-I", OUT]
     objs = []
 
     def compile_one(src):

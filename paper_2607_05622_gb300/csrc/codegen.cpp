@@ -12,15 +12,18 @@
 // device, so the same text is checked on the CPU and compiled for the GPU.
 //
 // Output, for a class (la lb|lc ld) with deriv 0/1 and a name prefix P:
-//   template <typename Real> LTJK_HD inline void P_vrr(const Real *base,
+//   template <typename Real> LTJK_GEN_FN void P_vrr(const Real *base,
 //       const Real *cf, const Real *h, Real *acc);
 //     one primitive quartet: base[m] = [00|00]^(m), m = 0..ltot; cf the
 //     kNumCoef coefficients of CoefSlot; h the 3 nh tables n/(2 zeta),
 //     n/(2 eta), n/(2 (zeta+eta)); acc[acc_total] accumulated in place.
-//   template <typename Real> LTJK_HD inline void P_hrr(const Real *acc,
+//   template <typename Real> LTJK_GEN_FN void P_hrr(const Real *acc,
 //       const Real *X, Real *out);
 //     contracted accumulators -> output tiles out[tile * nout + o]; X[0..2] =
 //     A - B, X[3..5] = C - D.
+// LTJK_GEN_FN is the function qualifier, defined by whoever includes the
+// emitted text (inline host+device code for the CPU checks, forced-inline
+// device code in the library).
 #include <map>
 #include <sstream>
 #include <stdexcept>
@@ -66,7 +69,7 @@ std::string emit_class_source(const ProgramSet &ps, int la, int lb, int lc, int 
     << p.nout << "\n";
 
   // ---- vertical recurrence and accumulation, one primitive quartet
-  o << "template <typename Real>\nLTJK_HD inline void " << prefix
+  o << "template <typename Real>\nLTJK_GEN_FN void " << prefix
     << "_vrr(const Real *__restrict__ base, const Real *__restrict__ cf, const Real *__restrict__ h,\n"
     << "    Real *__restrict__ acc) {\n";
   o << "#ifndef __CUDA_ARCH__\n  using std::fma;\n#endif\n";
@@ -128,7 +131,7 @@ std::string emit_class_source(const ProgramSet &ps, int la, int lb, int lc, int 
   o << "}\n\n";
 
   // ---- horizontal recurrence on the contracted accumulators, every tile
-  o << "template <typename Real>\nLTJK_HD inline void " << prefix
+  o << "template <typename Real>\nLTJK_GEN_FN void " << prefix
     << "_hrr(const Real *__restrict__ acc, const Real *__restrict__ X, Real *__restrict__ out) {\n";
   o << "#ifndef __CUDA_ARCH__\n  using std::fma;\n#endif\n";
   for (int tile = 0; tile < p.ntile; ++tile) {

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <vector>
 
+#include "gen_kernel.cuh"
 #include "host.h"
 #include "kernels.cuh"
 
@@ -29,7 +30,8 @@ namespace {
 
 std::atomic<unsigned long long> g_launches{0};  // kernels launched by this library
 
-constexpr int kKetChunk = 16;            // most ket pairs per work item
+constexpr int kKetChunk = 16;            // most ket pairs per work item (interpreted kernel)
+constexpr int kGenKetChunk = 32;         // most ket pairs per work item (class-specialised kernel)
 constexpr long long kTargetItems = 152 * 24;  // work items a class should offer the GPU
 constexpr int kSideStreams = 4;          // class launches of one build run on these concurrently
 constexpr int kSmemBudget = 200 * 1024;  // bytes of shared memory per CTA we plan for
@@ -82,12 +84,34 @@ struct ClassWork {
   int n64 = 0, n32 = 0;
 };
 
+// Double-float pair (hi, lo) of a double: hi = nearest float, lo = nearest
+// float to the remainder.
+float2 split2(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
+// Streaming multiprocessors of the current device (grid sizing).
+int num_sms() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+  cache[dev] = n;
+  return n;
+}
+
 // Programs are generated once per process and uploaded once per device.
 struct ProgramCache {
   std::mutex mu;
   bool built = false;
   ProgramSet ps;
-  std::map<int, std::shared_ptr<DevBuf>> vrr, hrr, acc, lev, tiles, boys;
+  std::map<int, std::shared_ptr<DevBuf>> vrr, hrr, acc, lev, tiles, boys, boys2;
 };
 ProgramCache g_prog;
 
@@ -105,7 +129,7 @@ int program_set(const ProgramSet **ps) {
   return LTJK_OK;
 }
 
-int device_programs(int dev, DevProgs *out, const double **boys) {
+int device_programs(int dev, DevProgs *out, const double **boys, const float2 **boys2) {
   const ProgramSet *ps;
   int rc = program_set(&ps);
   if (rc) return rc;
@@ -130,6 +154,24 @@ int device_programs(int dev, DevProgs *out, const double **boys) {
         }
       }
     if ((rc = b->upload(tab))) return rc;
+    // double-float table: row k (T_k = k/16) holds F_{m+j}(T_k)/j! for
+    // m = 0..kBoysMaxM, then e^{-T_k}/j!, j < kBoysDfTaylor
+    const int nraw = kBoysDfOrders + kBoysDfTaylor - 1;
+    std::vector<double> raw2((size_t)kBoysDfRows * nraw);
+    boys_table(kBoysDfRows, nraw, 1.0 / 16, raw2.data());
+    std::vector<float2> tab2((size_t)kBoysDfRows * kBoysDfRow);
+    for (int k = 0; k < kBoysDfRows; ++k) {
+      double fact = 1.0;
+      for (int j = 0; j < kBoysDfTaylor; ++j) {
+        if (j > 0) fact *= j;
+        for (int m = 0; m < kBoysDfOrders; ++m)
+          tab2[(size_t)k * kBoysDfRow + m * kBoysDfTaylor + j] = split2(raw2[(size_t)k * nraw + m + j] / fact);
+        tab2[(size_t)k * kBoysDfRow + kBoysDfOrders * kBoysDfTaylor + j] = split2(std::exp(-k / 16.0) / fact);
+      }
+    }
+    auto b2 = std::make_shared<DevBuf>();
+    if ((rc = b2->upload(tab2))) return rc;
+    g_prog.boys2[dev] = b2;
     double inv_odd[kBoysRaw + 2], half_n[2 * kMaxLDeriv + 4];
     for (int m = 0; m < kBoysRaw + 2; ++m) inv_odd[m] = 1.0 / (2 * m + 1);
     for (int n = 0; n < 2 * kMaxLDeriv + 4; ++n) half_n[n] = 0.5 * n;
@@ -148,6 +190,7 @@ int device_programs(int dev, DevProgs *out, const double **boys) {
   out->levels = g_prog.lev[dev]->as<int>();
   out->tiles = g_prog.tiles[dev]->as<TileProg>();
   *boys = g_prog.boys[dev]->as<double>();
+  *boys2 = g_prog.boys2[dev]->as<float2>();
   return LTJK_OK;
 }
 
@@ -218,6 +261,47 @@ int launch_class(const DevProgs &PR, const ClassLaunch &cl_in, const JobTable &T
   return LTJK_OK;
 }
 
+// Class-specialised J/K kernel of class (LA LB|LC LD): four warps per CTA, a
+// persistent grid of as many CTAs as fit on the device at once.
+template <typename Real, int LA, int LB, int LC, int LD>
+int launch_gen_cls(const JobTable &T, cudaStream_t st) {
+  if (T.total <= 0) return LTJK_OK;
+  constexpr int NOUT = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD);
+  constexpr int kWarps = 4;
+  const size_t smem = gen_warp_smem<NOUT, Real>() * kWarps;
+  static std::atomic<int> ctas_per_sm{0};  // per instantiation
+  auto kern = gen_jk_kernel<Real, LA, LB, LC, LD>;
+  if (ctas_per_sm.load() == 0) {
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int n = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * kWarps, smem));
+    ctas_per_sm.store(std::max(n, 1));
+  }
+  const int ctas_needed = (T.total + kWarps - 1) / kWarps;
+  const int grid = std::min(ctas_needed, num_sms() * ctas_per_sm.load());
+  kern<<<grid, 32 * kWarps, smem, st>>>(T);
+  CUDA_TRY(cudaGetLastError());
+  g_launches += 1;
+  return LTJK_OK;
+}
+
+template <typename Real>
+int launch_gen(int la, int lb, int lc, int ld, const JobTable &T, cudaStream_t st) {
+#define LTJK_GEN_CASE(A_, B_, C_, D_) \
+  if (la == A_ && lb == B_ && lc == C_ && ld == D_) return launch_gen_cls<Real, A_, B_, C_, D_>(T, st);
+  LTJK_GEN_CLASSES(LTJK_GEN_CASE)
+#undef LTJK_GEN_CASE
+  return set_error(LTJK_EINVAL, "no class-specialised kernel for (%d%d|%d%d)", la, lb, lc, ld);
+}
+
+// J/K launch of one class: the class-specialised kernel where the class has
+// one, the interpreted kernel otherwise.
+template <typename Real>
+int launch_jk(const ClassProg &p, const DevProgs &PR, const JobTable &T, cudaStream_t st) {
+  if (gen_class(p.la, p.lb, p.lc, p.ld)) return launch_gen<Real>(p.la, p.lb, p.lc, p.ld, T, st);
+  return launch_class<Real, kJK>(PR, make_launch(p, sizeof(Real)), T, st);
+}
+
 // A launch over one job.
 JobTable single_job(const DevBasis &B, const JKArgs &a, const WorkItem *items, int n) {
   JobTable T;
@@ -248,9 +332,10 @@ struct ltjk_ctx {
   std::map<std::pair<int, int>, int> pair_of;  // canonical (a,b) -> sorted pair index
   // device data
   DevBuf d_ctr, d_l, d_ao, d_atom, d_pair_sh, d_pair_pp0, d_pair_npp, d_pp_zeta, d_pp_izeta, d_pp_P,
-      d_pp_pref, d_pp_a, d_pp_b, d_pp2, d_ctr2;
+      d_pp_pref, d_pp_a, d_pp_b, d_pp2, d_ctr2, d_ppg2, d_ppg;
   DevProgs progs{};
   const double *boys = nullptr;
+  const float2 *boys2 = nullptr;
   std::vector<std::unique_ptr<ClassWork>> work;       // value build
   std::vector<std::unique_ptr<ClassWork>> work_grad;  // gradient (same screening)
   DevBuf scratch;
@@ -286,6 +371,9 @@ struct ltjk_ctx {
     B.pp2 = d_pp2.as<float2>();
     B.ctr2 = d_ctr2.as<float2>();
     B.boys = boys;
+    B.ppg2 = d_ppg2.as<float2>();
+    B.ppg = d_ppg.as<double>();
+    B.boys2 = boys2;
     B.nao = nao;
     return B;
   }
@@ -305,12 +393,9 @@ struct HostPairs {
   std::vector<int> cls, pp0, npp;
   std::vector<double> zeta, izeta, P, pref, a, b;
   std::vector<float2> pp2;  // double-float copies, 8 per primitive pair
+  std::vector<double> ppg;  // specialised kernel: kPrimDf per primitive pair
+  std::vector<float2> ppg2;
 };
-
-float2 split2(double x) {
-  const float h = (float)x;
-  return make_float2(h, (float)(x - (double)h));
-}
 
 void build_pairs(const ltjk_ctx &c, const std::vector<int2> &order, HostPairs &hp) {
   const double pi = 3.14159265358979323846;
@@ -341,6 +426,11 @@ void build_pairs(const ltjk_ctx &c, const std::vector<int2> &order, HostPairs &h
                               (al * A[2] + be * B[2]) / z};
         for (double v : {z, 1.0 / z, Pv[0], Pv[1], Pv[2], s2pi52 * kab * ca * cb / z, al, be})
           hp.pp2.push_back(split2(v));
+        for (double v : {z, 1.0 / z, Pv[0], Pv[1], Pv[2], Pv[0] - A[0], Pv[1] - A[1], Pv[2] - A[2],
+                         s2pi52 * kab * ca * cb / z}) {
+          hp.ppg.push_back(v);
+          hp.ppg2.push_back(split2(v));
+        }
         ++kept;
       }
     hp.npp.push_back(kept);
@@ -354,7 +444,8 @@ int upload_pairs(ltjk_ctx &c, const HostPairs &hp) {
       (rc = c.d_pair_npp.upload(hp.npp)) || (rc = c.d_pp_zeta.upload(hp.zeta)) ||
       (rc = c.d_pp_izeta.upload(hp.izeta)) || (rc = c.d_pp_P.upload(hp.P)) ||
       (rc = c.d_pp_pref.upload(hp.pref)) || (rc = c.d_pp_a.upload(hp.a)) ||
-      (rc = c.d_pp_b.upload(hp.b)) || (rc = c.d_pp2.upload(hp.pp2)))
+      (rc = c.d_pp_b.upload(hp.b)) || (rc = c.d_pp2.upload(hp.pp2)) || (rc = c.d_ppg.upload(hp.ppg)) ||
+      (rc = c.d_ppg2.upload(hp.ppg2)))
     return rc;
   return LTJK_OK;
 }
@@ -499,8 +590,10 @@ int build_work(ltjk_ctx &c) {
       }
       // kets per work item: small enough that a class yields at least
       // kTargetItems items (heavy classes have few quartets), at most kKetChunk
-      auto chunk_of = [](long long total) {
-        return (int)std::max<long long>(1, std::min<long long>(kKetChunk, (total + kTargetItems - 1) / kTargetItems));
+      // (the class-specialised kernel runs one ket per lane: up to 32 per item)
+      const int cap = gen_class(cw->la, cw->lb, cw->lc, cw->ld) ? kGenKetChunk : kKetChunk;
+      auto chunk_of = [cap](long long total) {
+        return (int)std::max<long long>(1, std::min<long long>(cap, (total + kTargetItems - 1) / kTargetItems));
       };
       const int ch64 = chunk_of(tot64), ch32 = chunk_of(tot32);
       std::vector<WorkItem> i64, i32;
@@ -578,15 +671,19 @@ int launch_classes(ltjk_ctx *ctx, const JKArgs &a, cudaStream_t st) {
     if (w->n64) {
       cudaStream_t s2 = ctx->side[next++ % kSideStreams];
       const JobTable T = single_job(B, a, w->items64.as<WorkItem>(), w->n64);
-      rc = native ? launch_class<double, MODE>(ctx->progs, make_launch(p, sizeof(double)), T, s2)
-                  : launch_class<dflt, MODE>(ctx->progs, make_launch(p, sizeof(dflt)), T, s2);
+      if (MODE == kJK)
+        rc = native ? launch_jk<double>(p, ctx->progs, T, s2) : launch_jk<dflt>(p, ctx->progs, T, s2);
+      else
+        rc = native ? launch_class<double, MODE>(ctx->progs, make_launch(p, sizeof(double)), T, s2)
+                    : launch_class<dflt, MODE>(ctx->progs, make_launch(p, sizeof(dflt)), T, s2);
       if (rc) return rc;
     }
     if (w->n32) {
       cudaStream_t s2 = ctx->side[next++ % kSideStreams];
-      if ((rc = launch_class<float, MODE>(ctx->progs, make_launch(p, sizeof(float)),
-                                          single_job(B, a, w->items32.as<WorkItem>(), w->n32), s2)))
-        return rc;
+      const JobTable T = single_job(B, a, w->items32.as<WorkItem>(), w->n32);
+      rc = MODE == kJK ? launch_jk<float>(p, ctx->progs, T, s2)
+                       : launch_class<float, MODE>(ctx->progs, make_launch(p, sizeof(float)), T, s2);
+      if (rc) return rc;
     }
   }
   // join
@@ -658,7 +755,7 @@ int ltjk_context_create(const ltjk_basis *bs, const ltjk_opts *opts, ltjk_ctx **
   // the basis is checked on the host before the first CUDA call
   CUDA_TRY(cudaSetDevice(c->device));
   int rc;
-  if ((rc = device_programs(c->device, &c->progs, &c->boys))) return rc;
+  if ((rc = device_programs(c->device, &c->progs, &c->boys, &c->boys2))) return rc;
   CUDA_TRY(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
   for (int k = 0; k < kSideStreams; ++k) {
     CUDA_TRY(cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking));

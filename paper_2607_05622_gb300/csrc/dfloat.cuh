@@ -237,6 +237,17 @@ __device__ __forceinline__ double acc_final(DotAcc acc) {
   return df_to_double(s, err);
 }
 
+// Add an accumulated sum into a binary64 element with L2 reductions.  A
+// double-float sum goes in as its two words, each converted exactly: the L2
+// adds them in binary64, so no renormalisation or integer rounding of the
+// pair is needed (two reductions instead of ~25 instructions of conversion).
+__device__ __forceinline__ void red_add(double *p, double acc) { atomicAdd(p, acc); }
+__device__ __forceinline__ void red_add(double *p, float acc) { atomicAdd(p, f2d_bits(acc)); }
+__device__ __forceinline__ void red_add(double *p, DotAcc acc) {
+  atomicAdd(p, f2d_bits(acc.hi));
+  atomicAdd(p, f2d_bits(acc.lo));
+}
+
 template <typename Real>
 __device__ __forceinline__ Real zero_real() { return Real(0); }
 template <>

@@ -56,6 +56,86 @@ __device__ __forceinline__ void boys_eval(int mmax, double T, const double *__re
   }
 }
 
+__device__ __forceinline__ dflt df_load(const float2 *p) {
+  const float2 v = __ldg(p);
+  return dflt(v.x, v.y);
+}
+
+// ----------------------------------------------- double-float Boys function
+// F_m(T) = int_0^1 u^{2m} exp(-T u^2) du on the FP32 pipe.  For T < 60:
+// Taylor expansion about the nearest point T_k = k/16 of a table of
+// F_{m+j}(T_k)/j! and e^{-T_k}/j! (j < 7, |T - T_k| <= 1/32, truncation below
+// 6e-15 relative); low orders (m <= 1) are expanded directly, higher ones
+// expand F_mmax and e^{-T} and descend with F_m = (2T F_{m+1} + e^{-T})/(2m+1)
+// (stable downwards).  For T >= 60: F_0 = (1/2) sqrt(pi/T) and
+// F_{m+1} = (2m+1)/(2T) F_m, the e^{-T} terms (below e^{-60} = 9e-27 of F_0,
+// under 1e-14 relative up to m = 14) dropped.  No exp() call: the table
+// carries the exponential.
+constexpr int kBoysDfTaylor = 7;
+constexpr int kBoysDfRows = 961;                  // T_k = k/16, k = 0..960
+constexpr int kBoysDfOrders = kBoysMaxM + 1;      // F_0 .. F_kBoysMaxM, then e^{-T}
+constexpr int kBoysDfRow = (kBoysDfOrders + 1) * kBoysDfTaylor;  // float2 per row
+constexpr float kBoysDfTmax = 60.0f;
+
+__device__ __forceinline__ dflt df_horner7(const float2 *__restrict__ c, dflt x) {
+  dflt f = df_load(c + kBoysDfTaylor - 1);
+#pragma unroll
+  for (int j = kBoysDfTaylor - 2; j >= 0; --j) f = fma(f, x, df_load(c + j));
+  return f;
+}
+
+template <int MMAX>
+__device__ __forceinline__ void boys_df(dflt T, const float2 *__restrict__ tab, dflt *F) {
+  if (T.hi < kBoysDfTmax) {
+    const int k = min(max(__float2int_rn(T.hi * 16.0f), 0), kBoysDfRows - 1);
+    // x = T_k - T: the leading difference is exact (Sterbenz), then renormalised
+    const float xh = __fsub_rn((float)k * 0.0625f, T.hi);
+    const float s = __fadd_rn(xh, -T.lo);
+    const float bb = __fsub_rn(s, xh);
+    const dflt x(s, __fadd_rn(__fsub_rn(xh, __fsub_rn(s, bb)), __fsub_rn(-T.lo, bb)));
+    const float2 *row = tab + (size_t)k * kBoysDfRow;
+    if (MMAX <= 1) {
+#pragma unroll
+      for (int m = 0; m <= MMAX; ++m) F[m] = df_horner7(row + m * kBoysDfTaylor, x);
+    } else {
+      F[MMAX] = df_horner7(row + MMAX * kBoysDfTaylor, x);
+      const dflt e = df_horner7(row + kBoysDfOrders * kBoysDfTaylor, x);
+      const dflt T2(2.0f * T.hi, 2.0f * T.lo);
+#pragma unroll
+      for (int m = MMAX - 1; m >= 0; --m) F[m] = fma(T2, F[m + 1], e) * dflt(1.0 / (2 * m + 1));
+    }
+  } else {
+    const dflt r = df_recip(T);
+    F[0] = df_sqrt(r) * dflt(0.88622692545275801365);  // (1/2) sqrt(pi)
+#pragma unroll
+    for (int m = 0; m < MMAX; ++m) F[m + 1] = df_mulf(F[m] * r, 0.5f * (2 * m + 1));
+  }
+}
+
+// Runtime-order variant for the interpreted kernel's set-up.
+__device__ __forceinline__ void boys_df_rt(int mmax, dflt T, const float2 *__restrict__ tab, dflt *F) {
+  if (T.hi < kBoysDfTmax) {
+    const int k = min(max(__float2int_rn(T.hi * 16.0f), 0), kBoysDfRows - 1);
+    const float xh = __fsub_rn((float)k * 0.0625f, T.hi);
+    const float s = __fadd_rn(xh, -T.lo);
+    const float bb = __fsub_rn(s, xh);
+    const dflt x(s, __fadd_rn(__fsub_rn(xh, __fsub_rn(s, bb)), __fsub_rn(-T.lo, bb)));
+    const float2 *row = tab + (size_t)k * kBoysDfRow;
+    if (mmax <= 1) {
+      for (int m = 0; m <= mmax; ++m) F[m] = df_horner7(row + m * kBoysDfTaylor, x);
+    } else {
+      F[mmax] = df_horner7(row + mmax * kBoysDfTaylor, x);
+      const dflt e = df_horner7(row + kBoysDfOrders * kBoysDfTaylor, x);
+      const dflt T2(2.0f * T.hi, 2.0f * T.lo);
+      for (int m = mmax - 1; m >= 0; --m) F[m] = fma(T2, F[m + 1], e) * dflt(c_inv_odd[m]);
+    }
+  } else {
+    const dflt r = df_recip(T);
+    F[0] = df_sqrt(r) * dflt(0.88622692545275801365);
+    for (int m = 0; m < mmax; ++m) F[m + 1] = df_mulf(F[m] * r, 0.5f * (2 * m + 1));
+  }
+}
+
 // --------------------------------------------------------------- layouts
 struct DevBasis {
   // shells
@@ -70,6 +150,12 @@ struct DevBasis {
   const float2 *pp2;     // the same as double-float pairs: [npp][8] = zeta, 1/zeta, P, pref, alpha, beta
   const float2 *ctr2;    // shell centres as double-float pairs [nshells][3]
   const double *boys;    // [kBoysRows][kBoysCols]
+  // class-specialised kernel: primitive pairs as double-float [npp][kPrimDf] =
+  // zeta, 1/zeta, P[3], P - A[3], prefactor (A the centre of the pair's first
+  // shell), the same in binary64 [npp][kPrimDf], and the double-float Boys table
+  const float2 *ppg2;
+  const double *ppg;
+  const float2 *boys2;
   int nao;
 };
 
@@ -207,10 +293,6 @@ __device__ __forceinline__ void stage1<double>(const DevBasis &B, const ClassPro
   }
 }
 
-__device__ __forceinline__ dflt df_load(const float2 *p) {
-  const float2 v = __ldg(p);
-  return dflt(v.x, v.y);
-}
 template <typename Real>
 __device__ __forceinline__ Real df_cvt(dflt x);
 template <>
@@ -218,8 +300,7 @@ __device__ __forceinline__ dflt df_cvt<dflt>(dflt x) { return x; }
 template <>
 __device__ __forceinline__ float df_cvt<float>(dflt x) { return df_to_float(x); }
 
-// Double-float throughout on the FP32 pipe, except the Boys function (IEEE
-// FP64, its argument rounded once from double-float to double).
+// Double-float throughout on the FP32 pipe, the Boys function included.
 template <typename Real>
 __device__ __forceinline__ void stage1(const DevBasis &B, const ClassProg &p, Real *e, int ia, int ic,
                                        int2 sab, int2 scd) {
@@ -236,10 +317,10 @@ __device__ __forceinline__ void stage1(const DevBasis &B, const ClassProg &p, Re
     const dflt d = P[x] - Q[x];
     PQ2 = fma(d, d, PQ2);
   }
-  double F[kBoysMaxM + 1];
-  boys_eval(p.ltot, to_double(rho * PQ2), B.boys, F);
+  dflt F[kBoysMaxM + 1];
+  boys_df_rt(p.ltot, rho * PQ2, B.boys2, F);
   const dflt pre = df_load(pa + 5) * df_load(pc + 5) * df_sqrt(isum);
-  for (int m = 0; m <= p.ltot; ++m) e[m] = df_cvt<Real>(pre * dflt(F[m]));
+  for (int m = 0; m <= p.ltot; ++m) e[m] = df_cvt<Real>(pre * F[m]);
   Real *cf = e + p.ltot + 1;
   for (int x = 0; x < 3; ++x) {
     const dflt W = (zeta * P[x] + eta * Q[x]) * isum;

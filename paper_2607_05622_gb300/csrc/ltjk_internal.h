@@ -20,7 +20,7 @@ constexpr int kBoysMaxM = 4 * kMaxLDeriv + 2;
 #define LTJK_HD
 #endif
 
-LTJK_HD inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+LTJK_HD constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 
 // Coefficient slots of one primitive quartet, stored after its base values
 // [00|00]^(m), m = 0..ltot, in the per-warp primitive table.
@@ -106,6 +106,18 @@ inline int pair_class(int la, int lb) { return la * (la + 1) / 2 + lb; }
 constexpr int kNumPairClass = (kMaxL + 1) * (kMaxL + 2) / 2;
 inline int quartet_index(int la, int lb, int lc, int ld, int deriv) {
   return (deriv * kNumPairClass + pair_class(la, lb)) * kNumPairClass + pair_class(lc, ld);
+}
+
+// Value classes whose J/K digestion runs in the class-specialised kernel: one
+// thread holds a whole contracted quartet (accumulators, recurrence
+// temporaries and output block in registers), so only classes whose
+// straight-line code fits the register file with room for several warps per
+// scheduler are listed (total angular momentum up to 3: at most 168
+// registers in double-float; (ds|ds) and (dd|ss) need 240-255 and ran slower
+// than in the interpreted kernel).  The rest run in the warp-cooperative
+// interpreted kernel.
+LTJK_HD constexpr bool gen_class(int la, int lb, int lc, int ld) {
+  return la >= lb && lc >= ld && (la > lc || (la == lc && lb >= ld)) && la + lb + lc + ld <= 3;
 }
 
 void build_programs(ProgramSet &ps);

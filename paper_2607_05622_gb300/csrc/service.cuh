@@ -160,11 +160,11 @@ int ltjk_service::step(std::vector<SvcJob *> &run) {
           cudaStream_t st = side[q % kSideStreams];
           if (mode == 0) {
             if (prec == 0)
-              launch_class<dflt, kJK>(PR, make_launch(*prog, sizeof(dflt)), T, st);
+              launch_jk<dflt>(*prog, PR, T, st);
             else if (prec == 1)
-              launch_class<float, kJK>(PR, make_launch(*prog, sizeof(float)), T, st);
+              launch_jk<float>(*prog, PR, T, st);
             else
-              launch_class<double, kJK>(PR, make_launch(*prog, sizeof(double)), T, st);
+              launch_jk<double>(*prog, PR, T, st);
           } else {
             if (prec == 0)
               launch_class<dflt, kGrad>(PR, make_launch(*prog, sizeof(dflt)), T, st);

@@ -18,7 +18,7 @@ int main(int argc, char **argv) {
   build_programs(ps);
   std::ofstream f(argv[1]);
   f << "// generated by tests/codegen_emit.cpp\n#pragma once\n#include <cmath>\n";
-  f << "#ifndef LTJK_HD\n#define LTJK_HD\n#endif\n\n";
+  f << "#ifndef LTJK_HD\n#define LTJK_HD\n#endif\n#define LTJK_GEN_FN LTJK_HD inline\n\n";
   std::string table;
   for (int la = 0; la <= lmax; ++la)
     for (int lb = 0; lb <= la; ++lb)
