@@ -12,15 +12,16 @@
 // device, so the same text is checked on the CPU and compiled for the GPU.
 //
 // Output, for a class (la lb|lc ld) with deriv 0/1 and a name prefix P:
-//   template <typename Real> LTJK_GEN_FN void P_vrr(const Real *base,
+//   template <typename Real, int AS = 1> LTJK_GEN_FN void P_vrr(const Real *base,
 //       const Real *cf, const Real *h, Real *acc);
 //     one primitive quartet: base[m] = [00|00]^(m), m = 0..ltot; cf the
 //     kNumCoef coefficients of CoefSlot; h the 3 nh tables n/(2 zeta),
-//     n/(2 eta), n/(2 (zeta+eta)); acc[acc_total] accumulated in place.
-//   template <typename Real> LTJK_GEN_FN void P_hrr(const Real *acc,
-//       const Real *X, Real *out);
-//     contracted accumulators -> output tiles out[tile * nout + o]; X[0..2] =
-//     A - B, X[3..5] = C - D.
+//     n/(2 eta), n/(2 (zeta+eta)); accumulator i, acc[AS * i], accumulated in
+//     place (AS > 1: one column of a lane-interleaved shared-memory block).
+//   template <typename Real, int AS = 1, int OS = 1> LTJK_GEN_FN void P_hrr(
+//       const Real *acc, const Real *X, Real *out);
+//     contracted accumulators acc[AS * i] -> output tiles out[OS * (tile *
+//     nout + o)]; X[0..2] = A - B, X[3..5] = C - D.
 // LTJK_GEN_FN is the function qualifier, defined by whoever includes the
 // emitted text (inline host+device code for the CPU checks, forced-inline
 // device code in the library).
@@ -69,7 +70,7 @@ std::string emit_class_source(const ProgramSet &ps, int la, int lb, int lc, int 
     << p.nout << "\n";
 
   // ---- vertical recurrence and accumulation, one primitive quartet
-  o << "template <typename Real>\nLTJK_GEN_FN void " << prefix
+  o << "template <typename Real, int AS = 1>\nLTJK_GEN_FN void " << prefix
     << "_vrr(const Real *__restrict__ base, const Real *__restrict__ cf, const Real *__restrict__ h,\n"
     << "    Real *__restrict__ acc) {\n";
   o << "#ifndef __CUDA_ARCH__\n  using std::fma;\n#endif\n";
@@ -122,7 +123,7 @@ std::string emit_class_source(const ProgramSet &ps, int la, int lb, int lc, int 
     const AccInstr &in = ps.acc[k];
     const Val v = get(in.slot);
     if (v.zero()) continue;
-    const std::string a = "acc[" + std::to_string(in.acc) + "]";
+    const std::string a = "acc[AS * " + std::to_string(in.acc) + "]";
     if (in.chan == 0)
       o << "  " << a << " += " << v.expr << ";\n";
     else
@@ -131,7 +132,7 @@ std::string emit_class_source(const ProgramSet &ps, int la, int lb, int lc, int 
   o << "}\n\n";
 
   // ---- horizontal recurrence on the contracted accumulators, every tile
-  o << "template <typename Real>\nLTJK_GEN_FN void " << prefix
+  o << "template <typename Real, int AS = 1, int OS = 1>\nLTJK_GEN_FN void " << prefix
     << "_hrr(const Real *__restrict__ acc, const Real *__restrict__ X, Real *__restrict__ out) {\n";
   o << "#ifndef __CUDA_ARCH__\n  using std::fma;\n#endif\n";
   for (int tile = 0; tile < p.ntile; ++tile) {
@@ -140,7 +141,7 @@ std::string emit_class_source(const ProgramSet &ps, int la, int lb, int lc, int 
     auto hget = [&](int s) -> Val {
       auto it = hs.find(s);
       if (it != hs.end()) return it->second;
-      if (s < p.acc_total) return Val{"acc[" + std::to_string(s) + "]"};
+      if (s < p.acc_total) return Val{"acc[AS * " + std::to_string(s) + "]"};
       if (s == p.acc_total) return Val{};
       throw std::runtime_error("emit_class_source: HRR slot read before written");
     };
@@ -173,7 +174,7 @@ std::string emit_class_source(const ProgramSet &ps, int la, int lb, int lc, int 
     }
     for (int q = 0; q < T.nout; ++q) {
       const Val v = hget(T.out_base + q);
-      o << "    out[" << tile * T.nout + q << "] = " << (v.zero() ? "Real(0)" : v.expr) << ";\n";
+      o << "    out[OS * " << tile * T.nout + q << "] = " << (v.zero() ? "Real(0)" : v.expr) << ";\n";
     }
     o << "  }\n";
   }

@@ -267,8 +267,9 @@ template <typename Real, int LA, int LB, int LC, int LD>
 int launch_gen_cls(const JobTable &T, cudaStream_t st) {
   if (T.total <= 0) return LTJK_OK;
   constexpr int NOUT = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD);
+  constexpr int NACC = kGenSmemAcc<LA, LB, LC, LD> ? GenClass<LA, LB, LC, LD>::kAcc : 0;
   constexpr int kWarps = 4;
-  const size_t smem = gen_warp_smem<NOUT, Real>() * kWarps;
+  const size_t smem = gen_warp_smem<NOUT, NACC, Real>() * kWarps;
   static std::atomic<int> ctas_per_sm{0};  // per instantiation
   auto kern = gen_jk_kernel<Real, LA, LB, LC, LD>;
   if (ctas_per_sm.load() == 0) {

@@ -137,14 +137,21 @@ __device__ __forceinline__ void gen_setup_64(const Prim64 &a, const Prim64 &c, c
   }
 }
 
-// Contracted block of quartet (bra pair ip | ket pair jp) into out[].
-template <typename Real, int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void gen_quartet(const DevBasis &B, int ip, int jp, Real *out) {
+// Classes whose contracted accumulators and output block live in shared
+// memory (one column per lane) rather than in registers: with the recurrence
+// temporaries, the accumulators of a total angular momentum of 4 or more
+// would need 250+ registers in double-float.
+template <int LA, int LB, int LC, int LD>
+constexpr bool kGenSmemAcc = LA + LB + LC + LD >= 4;
+
+// Accumulate the contracted values [e0|f0] of quartet (bra pair ip | ket
+// pair jp) into acc[AS * i] over all primitive quartets (acc zeroed first).
+template <typename Real, int LA, int LB, int LC, int LD, int AS>
+__device__ __forceinline__ void gen_contract(const DevBasis &B, int ip, int jp, Real *acc) {
   using G = GenClass<LA, LB, LC, LD>;
   constexpr int LT = G::kLtot, NH = G::kNh;
-  Real acc[G::kAcc];
 #pragma unroll
-  for (int t = 0; t < G::kAcc; ++t) acc[t] = zero_real<Real>();
+  for (int t = 0; t < G::kAcc; ++t) acc[AS * t] = zero_real<Real>();
   const int pp0 = __ldg(B.pair_pp0 + ip), npp = __ldg(B.pair_npp + ip);
   const int qq0 = __ldg(B.pair_pp0 + jp), nqq = __ldg(B.pair_npp + jp);
   for (int ia = pp0; ia < pp0 + npp; ++ia) {
@@ -154,7 +161,7 @@ __device__ __forceinline__ void gen_quartet(const DevBasis &B, int ip, int jp, R
         const Prim64 pc = load_prim_64(B.ppg + (size_t)kPrimDf * ic);
         double base[LT + 1], cf[kNumCoef], h[3 * NH];
         gen_setup_64<LT, NH>(pa, pc, B.boys, base, cf, h);
-        G::template vrr<double>(base, cf, h, acc);
+        G::template vrr<double, AS>(base, cf, h, acc);
       }
     } else {
       const PrimDf pa = load_prim_df(B.ppg2 + (size_t)kPrimDf * ia);
@@ -162,10 +169,15 @@ __device__ __forceinline__ void gen_quartet(const DevBasis &B, int ip, int jp, R
         const PrimDf pc = load_prim_df(B.ppg2 + (size_t)kPrimDf * ic);
         Real base[LT + 1], cf[kNumCoef], h[3 * NH];
         gen_setup_df<Real, LT, NH>(pa, pc, B.boys2, base, cf, h);
-        G::template vrr<Real>(base, cf, h, acc);
+        G::template vrr<Real, AS>(base, cf, h, acc);
       }
     }
   }
+}
+
+// Horizontal recurrence of quartet (ip | jp): acc[AS * i] -> out[OS * o].
+template <typename Real, int LA, int LB, int LC, int LD, int AS, int OS>
+__device__ __forceinline__ void gen_transfer(const DevBasis &B, int ip, int jp, const Real *acc, Real *out) {
   const int2 sab = __ldg(B.pair_sh + ip), scd = __ldg(B.pair_sh + jp);
   Real X[6];
 #pragma unroll
@@ -178,7 +190,7 @@ __device__ __forceinline__ void gen_quartet(const DevBasis &B, int ip, int jp, R
       X[3 + x] = df_cvt<Real>(df_load(B.ctr2 + 3 * scd.x + x) - df_load(B.ctr2 + 3 * scd.y + x));
     }
   }
-  G::template hrr<Real>(acc, X, out);
+  GenClass<LA, LB, LC, LD>::template hrr<Real, AS, OS>(acc, X, out);
 }
 
 // ------------------------------------------------------------ digestion
@@ -238,9 +250,12 @@ __device__ __forceinline__ void gen_place_n(const Real *Ik, const Real *M, doubl
 }
 
 // ---------------------------------------------------------------- kernel
-template <int NOUT, typename Real>
+// Shared memory of one warp: the integral blocks of its 32 kets [NOUT][32],
+// the kets' AO offsets [32], and (shared-memory classes) the contracted
+// accumulators [NACC][32].
+template <int NOUT, int NACC, typename Real>
 __host__ __device__ constexpr size_t gen_warp_smem() {
-  return ((size_t)NOUT * 32 * sizeof(Real) + 32 * sizeof(int2) + 15) / 16 * 16;
+  return ((size_t)(NOUT + NACC) * 32 * sizeof(Real) + 32 * sizeof(int2) + 15) / 16 * 16;
 }
 
 template <typename Real, int LA, int LB, int LC, int LD>
@@ -248,12 +263,15 @@ __global__ void __launch_bounds__(128, 4) gen_jk_kernel(const __grid_constant__ 
   constexpr int NA = (LA + 1) * (LA + 2) / 2, NB = (LB + 1) * (LB + 2) / 2;
   constexpr int NC = (LC + 1) * (LC + 2) / 2, ND = (LD + 1) * (LD + 2) / 2;
   constexpr int NOUT = NA * NB * NC * ND;
+  constexpr bool SMEM = kGenSmemAcc<LA, LB, LC, LD>;
+  constexpr int NACC = SMEM ? GenClass<LA, LB, LC, LD>::kAcc : 0;
   static_assert(NOUT == GenClass<LA, LB, LC, LD>::kOut, "generated block size");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  unsigned char *wbase = smem_raw + (size_t)warp * gen_warp_smem<NOUT, Real>();
+  unsigned char *wbase = smem_raw + (size_t)warp * gen_warp_smem<NOUT, NACC, Real>();
   Real *Ism = reinterpret_cast<Real *>(wbase);                              // [NOUT][32]
-  int2 *kinfo = reinterpret_cast<int2 *>(wbase + (size_t)NOUT * 32 * sizeof(Real));  // [32]
+  Real *Asm = Ism + NOUT * 32;                                              // [NACC][32]
+  int2 *kinfo = reinterpret_cast<int2 *>(wbase + (size_t)(NOUT + NACC) * 32 * sizeof(Real));  // [32]
   for (int it = blockIdx.x * nwarps + warp; it < T.total; it += gridDim.x * nwarps) {
     int jb = 0;
     while (jb + 1 < T.njobs && it >= T.j[jb + 1].first) ++jb;
@@ -267,15 +285,23 @@ __global__ void __launch_bounds__(128, 4) gen_jk_kernel(const __grid_constant__ 
     const int a0 = __ldg(B.sh_ao + sab.x), b0 = __ldg(B.sh_ao + sab.y);
     if (lane < nk) {
       const int jp = W.k0 + lane;
-      Real out[NOUT];
-      gen_quartet<Real, LA, LB, LC, LD>(B, W.bra, jp, out);
       const int2 scd = __ldg(B.pair_sh + jp);
       float wf = 1.0f;  // degeneracy weight of the unique quartet
       if (sab.x == sab.y) wf *= 0.5f;
       if (scd.x == scd.y) wf *= 0.5f;
       if (W.bra == jp) wf *= 0.5f;
+      if constexpr (SMEM) {
+        gen_contract<Real, LA, LB, LC, LD, 32>(B, W.bra, jp, Asm + lane);
+        gen_transfer<Real, LA, LB, LC, LD, 32, 32>(B, W.bra, jp, Asm + lane, Ism + lane);
+#pragma unroll 4
+        for (int o = 0; o < NOUT; ++o) Ism[32 * o + lane] = scale_pow2(Ism[32 * o + lane], wf);
+      } else {
+        Real acc[GenClass<LA, LB, LC, LD>::kAcc], out[NOUT];
+        gen_contract<Real, LA, LB, LC, LD, 1>(B, W.bra, jp, acc);
+        gen_transfer<Real, LA, LB, LC, LD, 1, 1>(B, W.bra, jp, acc, out);
 #pragma unroll
-      for (int o = 0; o < NOUT; ++o) Ism[32 * o + lane] = scale_pow2(out[o], wf);
+        for (int o = 0; o < NOUT; ++o) Ism[32 * o + lane] = scale_pow2(out[o], wf);
+      }
       kinfo[lane] = make_int2(__ldg(B.sh_ao + scd.x), __ldg(B.sh_ao + scd.y));
     }
     __syncwarp();
@@ -324,11 +350,5 @@ __global__ void __launch_bounds__(128, 4) gen_jk_kernel(const __grid_constant__ 
   }
 }
 
-// Shared memory of one warp of class (la lb|lc ld), 0 if the class has no
-// specialised kernel.
-inline size_t gen_smem_per_warp(int la, int lb, int lc, int ld, size_t real_bytes) {
-  const size_t nout = (size_t)ncart(la) * ncart(lb) * ncart(lc) * ncart(ld);
-  return (nout * 32 * real_bytes + 32 * sizeof(int2) + 15) / 16 * 16;
-}
 
 }  // namespace ltjk

@@ -49,10 +49,10 @@ int main(int argc, char **argv) {
                   "  static constexpr int kAcc = " + std::to_string(p.acc_total) + ";\n" +
                   "  static constexpr int kOut = " + std::to_string(p.nout) + ";\n" +
                   "  static constexpr int kNh = " + std::to_string(p.nh) + ";\n" +
-                  "  template <typename Real>\n  static LTJK_GEN_FN void vrr(const Real *b, const Real *cf, "
-                  "const Real *h, Real *acc) {\n    " + name + "_vrr<Real>(b, cf, h, acc);\n  }\n" +
-                  "  template <typename Real>\n  static LTJK_GEN_FN void hrr(const Real *acc, const Real *X, "
-                  "Real *out) {\n    " + name + "_hrr<Real>(acc, X, out);\n  }\n};\n";
+                  "  template <typename Real, int AS = 1>\n  static LTJK_GEN_FN void vrr(const Real *b, const Real *cf, "
+                  "const Real *h, Real *acc) {\n    " + name + "_vrr<Real, AS>(b, cf, h, acc);\n  }\n" +
+                  "  template <typename Real, int AS = 1, int OS = 1>\n  static LTJK_GEN_FN void hrr(const Real *acc, "
+                  "const Real *X, Real *out) {\n    " + name + "_hrr<Real, AS, OS>(acc, X, out);\n  }\n};\n";
           list += " X(" + std::to_string(la) + ", " + std::to_string(lb) + ", " + std::to_string(lc) + ", " +
                   std::to_string(ld) + ")";
         }

@@ -109,15 +109,17 @@ inline int quartet_index(int la, int lb, int lc, int ld, int deriv) {
 }
 
 // Value classes whose J/K digestion runs in the class-specialised kernel: one
-// thread holds a whole contracted quartet (accumulators, recurrence
-// temporaries and output block in registers), so only classes whose
-// straight-line code fits the register file with room for several warps per
-// scheduler are listed (total angular momentum up to 3: at most 168
-// registers in double-float; (ds|ds) and (dd|ss) need 240-255 and ran slower
-// than in the interpreted kernel).  The rest run in the warp-cooperative
-// interpreted kernel.
+// thread evaluates a whole contracted quartet, so only classes whose
+// straight-line code fits 128 registers (four warps of 128 threads per SM
+// scheduler group) with at most a few hundred bytes of spills are listed:
+// total angular momentum up to 3 with everything in registers, and the
+// classes of total angular momentum 4 with at most 54 integrals ((dd|ss),
+// (ds|ds), (dp|ps), (ds|pp)) with their contracted accumulators and output
+// block in shared memory.  (pp|pp) and heavier classes spill kilobytes per
+// thread and run in the warp-cooperative interpreted kernel.
 LTJK_HD constexpr bool gen_class(int la, int lb, int lc, int ld) {
-  return la >= lb && lc >= ld && (la > lc || (la == lc && lb >= ld)) && la + lb + lc + ld <= 3;
+  return la >= lb && lc >= ld && (la > lc || (la == lc && lb >= ld)) &&
+         (la + lb + lc + ld <= 3 || (la + lb + lc + ld == 4 && ncart(la) * ncart(lb) * ncart(lc) * ncart(ld) <= 54));
 }
 
 void build_programs(ProgramSet &ps);
