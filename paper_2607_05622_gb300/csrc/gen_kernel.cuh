@@ -139,10 +139,10 @@ __device__ __forceinline__ void gen_setup_64(const Prim64 &a, const Prim64 &c, c
 
 // Classes whose contracted accumulators and output block live in shared
 // memory (one column per lane) rather than in registers: with the recurrence
-// temporaries, the accumulators of a total angular momentum of 4 or more
-// would need 250+ registers in double-float.
+// temporaries, the accumulators of a total angular momentum of 4 or more,
+// and of (pp|ps), would need 170-250 registers in double-float.
 template <int LA, int LB, int LC, int LD>
-constexpr bool kGenSmemAcc = LA + LB + LC + LD >= 4;
+constexpr bool kGenSmemAcc = LA + LB + LC + LD >= 4 || (LA == 1 && LB == 1 && LC == 1);
 
 // Accumulate the contracted values [e0|f0] of quartet (bra pair ip | ket
 // pair jp) into acc[AS * i] over all primitive quartets (acc zeroed first).

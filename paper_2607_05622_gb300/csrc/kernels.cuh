@@ -544,10 +544,10 @@ __device__ __forceinline__ void digest_place(const Real *__restrict__ I, const R
         acc3 = acc_fma(acc3, Ib[3][iv], m);
       }
     }
-    atomicAdd(Tblk + to[0], acc_final(acc0));
-    if (cnt > 1) atomicAdd(Tblk + to[1], acc_final(acc1));
-    if (cnt > 2) atomicAdd(Tblk + to[2], acc_final(acc2));
-    if (cnt > 3) atomicAdd(Tblk + to[3], acc_final(acc3));
+    red_add(Tblk + to[0], acc0);
+    if (cnt > 1) red_add(Tblk + to[1], acc1);
+    if (cnt > 2) red_add(Tblk + to[2], acc2);
+    if (cnt > 3) red_add(Tblk + to[3], acc3);
     q += 32;
     while (q >= nd) { q -= nd; ++grp; }
   }
