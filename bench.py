@@ -30,11 +30,7 @@ from paper_2607_05622_gb300 import workloads as W  # noqa: E402
 
 HBM_L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the class launches
-# of one J/K build of this workload, summed from one ncu capture of the current
-# quartet kernel (each launch replayed with flushed caches); None where not
-# captured.  Must be re-taken (or set to None) whenever the kernel changes.
-NCU_DRAM_BYTES_PER_BUILD = {"fp64": 359.6e6, "mixed": 608.2e6, "fp64-native": None}
+METRIC = "Laplace J/K builds/s (200-AO chain, 48 densities)"
 
 
 def measured_peaks():
@@ -45,11 +41,33 @@ def measured_peaks():
         return {}
 
 
-# FP64 / FP32 FMA peaks from unit counts and clocks: 152 SMs; per SM per clock
-# 128 FP32 FMA lanes and 2 FP64 FMA (the nominal 1.25 TFLOP/s FP64 at 2.07 GHz).
-def alu_peaks(sm_mhz):
+# Nominal FP64 / FP32 FMA peaks from unit counts and clocks (context only):
+# per SM per clock 128 FP32 FMA lanes and 2 FP64 FMA.
+def alu_peaks(sm_mhz, nsm=152):
     f = sm_mhz * 1e6
-    return {"fp32_tflops": 152 * 128 * 2 * f / 1e12, "fp64_tflops": 152 * 2 * 2 * f / 1e12}
+    return {"fp32_tflops": nsm * 128 * 2 * f / 1e12, "fp64_tflops": nsm * 2 * 2 * f / 1e12}
+
+
+def measure_alu_peaks(ltjk, torch, stream, reps=5):
+    """Arithmetic throughput on this GPU (ltjk_alu_peak: independent FMA chains
+    over 4 CTAs x 256 threads per SM), best of `reps` launches timed with CUDA
+    events, in TFLOP/s: binary32 FMA, binary64 FMA, double-float FMA (2 flops
+    each) and the digestion's double-float dot-product accumulation."""
+    out = {}
+    for kind, name in [(ltjk.ALU_FP32, "fp32_fma"), (ltjk.ALU_FP64, "fp64_fma"),
+                       (ltjk.ALU_DFLOAT_FMA, "dfloat_fma"), (ltjk.ALU_DFLOAT_DOT, "dfloat_dot")]:
+        ltjk.alu_peak(kind, stream)
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fl = ltjk.alu_peak(kind, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        out[name + "_tflops"] = fl / best / 1e12
+    return out
 
 
 class Clocks:
@@ -162,28 +180,49 @@ def cpu_oracle_sample(w, budget_s=20.0, nblocks=None):
     return {"value": nd / build_s, "unit": "builds/s", "cores": O.num_threads(), "kind": "oracle",
             "sample": f"{done} J+K shell-pair blocks x {nd} densities ({evals} ordered shell "
                       f"quartets in {el:.1f} s), extrapolated to {unique} unique quartets, unscreened",
-            "seconds": el}
+            "seconds": el, "evals": evals, "blocks": done}
+
+
+def bench_config(w, precision):
+    """The workload description both arms print."""
+    return {"workload": w.name, "precision": precision, "schwarz_tau": w.schwarz_tau,
+            "mixed_tau": 1e-6 if precision == "mixed" else None, "nao": w.mol.nao, "ndens": w.ndens,
+            "laplace_points": w.nlap, "l2": "flushed between timed steps (512 MB write)"}
 
 
 def run_reference(args, world, rank):
+    """The oracle as it stands, on the host cores: each step is a time-bounded
+    sample of the same workload (J and K blocks of random shell pairs,
+    extrapolated to the whole unscreened build); the value is the mean rate
+    over the timed steps."""
     if rank != 0:
         return
     w = W.config2()
-    cb = None
-    times = []
+    times, rates, evals, blocks = [], [], 0, 0
+    cores = None
     for step in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(w, nblocks=2)
-        if step >= args.warmup:
+        timed = step >= args.warmup
+        r = cpu_oracle_sample(w, budget_s=args.ref_seconds if timed else 1.0)
+        cores = r["cores"]
+        if timed:
             times.append(r["seconds"])
-            cb = r
-    vals = cb["value"]
-    line = {"impl": "reference", "metric": "Laplace J/K builds/s (200-AO chain, 48 densities)",
-            "value": vals, "unit": "builds/s", "n_gpus": args.gpus, "steps": args.steps,
+            rates.append(r["value"])
+            evals += r["evals"]
+            blocks += r["blocks"]
+    val = statistics.mean(rates)
+    cfg = bench_config(w, args.precision)
+    cfg["parallelism"] = "host cores (oracle)"
+    line = {"impl": "reference", "metric": METRIC,
+            "value": val, "unit": "builds/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "precision": "fp64 (CPU oracle)"},
-            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
-            "e2e": {"value": vals, "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": val, "unit": "builds/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{blocks} J+K shell-pair blocks x {w.ndens} densities over "
+                                       f"{args.steps} steps of ~{args.ref_seconds:.0f} s ({evals} ordered "
+                                       f"shell quartets), extrapolated to the unscreened build; the oracle "
+                                       f"computes in FP64"},
+            "e2e": {"value": val, "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
@@ -200,10 +239,23 @@ def _event_ms(torch, stream, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def measure_gradient(ltjk, torch, dev, local, stream, prec, reps=3):
+def mixed_peak(parts):
+    """Harmonic mix of peaks weighted by flop share: parts = [(flops, peak), ...];
+    the time-weighted peak of a path whose flops split over several units."""
+    tot = sum(f for f, _ in parts)
+    t = sum(f / p for f, p in parts if f > 0)
+    return tot / t if t > 0 else None
+
+
+def measure_gradient(ltjk, torch, dev, local, stream, prec, peaks, reps=3):
     """ERI-derivative contraction (Eq. jkderiv) on the 200-AO chain geometry with
-    16 separable symmetric terms: gradients/s, quartets/s, and the error against
-    an IEEE FP64 gradient on the same GPU."""
+    16 separable symmetric terms: gradients/s, quartets/s, the error against an
+    IEEE FP64 gradient on the same GPU, and its roofline: algorithmic flops per
+    gradient = the derivative-recurrence flop model + per kept Cartesian
+    integral 2R (Gamma formation, R terms) + 18 (nine derivative components),
+    against the measured peaks of the units they run on (derivative
+    recurrences double-float, or binary32 in mixed mode; Gamma and the
+    contraction binary64)."""
     wl = W.config4()
     ctx = ltjk.Context(wl.mol, schwarz_tau=wl.schwarz_tau, mixed_tau=1e-6, precision=prec, device=local)
     P = torch.from_numpy(wl.P).to(dev)
@@ -217,11 +269,70 @@ def measure_gradient(ltjk, torch, dev, local, stream, prec, reps=3):
     gmax = float(g64.abs().max())
     err = float((g - g64).abs().max())
     st = ctx.stats()
-    return {"workload": wl.name, "terms": int(P.shape[0]), "cJ": wl.cJ, "cK": wl.cK,
+    R = int(P.shape[0])
+    f_gamma = st["cart_integrals_kept"] * (2.0 * R + 18.0)
+    f_d64 = st["grad_eri_flops_fp64"]
+    f_d32 = st["grad_eri_flops"] - f_d64
+    if prec == ltjk.FP64_NATIVE:
+        parts = [(f_d64 + f_d32, peaks["fp64_fma_tflops"]), (f_gamma, peaks["fp64_fma_tflops"])]
+    else:
+        parts = [(f_d64, peaks["dfloat_fma_tflops"]), (f_d32, peaks["fp32_fma_tflops"]),
+                 (f_gamma, peaks["fp64_fma_tflops"])]
+    flops = f_gamma + f_d64 + f_d32
+    peak = mixed_peak(parts)
+    ach = flops / (ms / 1e3) / 1e12
+    return {"workload": wl.name, "terms": R, "cJ": wl.cJ, "cK": wl.cK,
             "grad_ms": ms, "gradients_per_s": 1e3 / ms,
             "quartets_per_s": st["quartets_kept"] / (ms / 1e3),
             "max_abs_vs_fp64": err, "rel_to_max_vs_fp64": err / gmax,
-            "sum_over_atoms_rel": float(g.sum(0).abs().max()) / gmax}
+            "sum_over_atoms_rel": float(g.sum(0).abs().max()) / gmax,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "algorithmic_flops": flops,
+                         "flops_split": {"derivative_recurrences_fp64_class": f_d64,
+                                         "derivative_recurrences_fp32": f_d32,
+                                         "gamma_and_contraction_binary64": f_gamma},
+                         "peak_source": "harmonic mix by flop share of the peaks measured in this run"}}
+
+
+def measure_config1(ltjk, torch, dev, local, stream, reps=20):
+    """The plain-FP64 single request of the 25-AO water-like molecule (8
+    pseudo-densities): builds/s in IEEE FP64 and FP64 class, and their
+    difference (relative to max)."""
+    w = W.config1()
+    xmin = 2.0 * (w.eps_vir.min() - w.eps_occ.max())
+    xmax = 2.0 * (w.eps_vir.max() - w.eps_occ.min())
+    t, _, _ = ltjk.laplace_quadrature(xmin, xmax, w.nlap)
+    out = {"workload": w.name, "nao": w.mol.nao, "ndens": w.ndens, "schwarz_tau": w.schwarz_tau}
+    res = {}
+    for name, prec in [("fp64_native", ltjk.FP64_NATIVE), ("fp64_class", ltjk.FP64)]:
+        ctx = ltjk.Context(w.mol, schwarz_tau=w.schwarz_tau, precision=prec, device=local)
+        D = ctx.pseudo_densities(torch.from_numpy(w.C_occ).to(dev), torch.from_numpy(w.C_vir).to(dev),
+                                 torch.from_numpy(w.eps_occ).to(dev), torch.from_numpy(w.eps_vir).to(dev),
+                                 torch.from_numpy(np.ascontiguousarray(w.X)).to(dev), t)
+        J, K = ctx.jk_build(D)
+        times = []
+        for _ in range(reps):
+            times.append(_event_ms(torch, stream, lambda: ctx.jk_build(D, J, K), 1))
+        ms = statistics.median(times)
+        res[name] = (J, K)
+        out[name] = {"build_ms": ms, "builds_per_s": w.ndens / (ms / 1e3), "quartets_kept": ctx.stats()["quartets_kept"]}
+    (J1, K1), (J2, K2) = res["fp64_native"], res["fp64_class"]
+    out["fp64_class_vs_native"] = {"J_max_rel_to_max": float((J2 - J1).abs().max() / J1.abs().max()),
+                                   "K_max_rel_to_max": float((K2 - K1).abs().max() / K1.abs().max())}
+    return out
+
+
+def measure_serving(ltjk, torch, dev, nreq=32, nao_hi=300):
+    """A short stream of the serving workload's shape (chain molecules with
+    AO counts log-uniform from 25 up to nao_hi, 8-16 Laplace points, 70 % J/K
+    and 30 % gradients, mixed precision, 150 GB budget) through the
+    continuous-batching service: p50/p99 latency at 0.8 of the measured
+    capacity, and the saturated throughput (every request at t = 0), each
+    against sequential plain FP64 on the same request list."""
+    import serving_bench as SB
+    paced = SB.run_stream(ltjk, torch, dev, nreq=nreq, nao_hi=nao_hi, load=0.8)
+    sat = SB.run_stream(ltjk, torch, dev, nreq=nreq, nao_hi=nao_hi, saturated=True)
+    return {"paced": paced, "saturated": sat}
 
 
 def measure_macrocycle(ltjk, torch, dev, local, stream, reps=2):
@@ -260,7 +371,7 @@ def measure_macrocycle(ltjk, torch, dev, local, stream, reps=2):
     return out
 
 
-def measure_next_rows(ltjk, torch, stream, ctx, w, J, K, Co, Cv, xmin, xmax, reps=5):
+def measure_next_rows(ltjk, torch, stream, ctx, w, J, K, Co, Cv, xmin, xmax, peaks, reps=5):
     """The rows either side of the build: the Laplace-Fock back-transform of the
     48 J/K pairs to the occupied-virtual block (Eq. laplacefock; FP64 GEMMs on
     the FP64 pipe) and the host-side minimax grid (Eq. laplace, Remez)."""
@@ -270,7 +381,7 @@ def measure_next_rows(ltjk, torch, stream, ctx, w, J, K, Co, Cv, xmin, xmax, rep
     ctx.laplace_fock(J, K, Co, Cv, 2.0, -1.0, F=F)
     ms = _event_ms(torch, stream, lambda: ctx.laplace_fock(J, K, Co, Cv, 2.0, -1.0, F=F), reps)
     flops = nd * (3.0 * N * N + 2.0 * N * N * nv + 2.0 * N * no * nv)
-    peak = alu_peaks(2070.0)["fp64_tflops"]
+    peak = peaks["fp64_fma_tflops"]
     t0 = time.perf_counter()
     tm, wm, em, conv = ltjk.laplace_minimax(xmin, xmax, w.nlap)
     mm_ms = 1e3 * (time.perf_counter() - t0)
@@ -282,7 +393,7 @@ def measure_next_rows(ltjk, torch, stream, ctx, w, J, K, Co, Cv, xmin, xmax, rep
                                 "converged": conv, "least_squares_max_rel_err": els}}
 
 
-def measure_cd(ltjk, torch, stream, ctx, w, D, J, K, Co, Cv, eo, ev, X, t, delta=1e-9, reps=2):
+def measure_cd(ltjk, torch, stream, ctx, w, D, J, K, Co, Cv, eo, ev, X, t, peaks, delta=1e-9, reps=2):
     """The Cholesky-factorised route on the same request (Eqs. cdfact, cdj,
     cdknonsym): factor set-up time and vectors, the J/K of the 48 pseudo-densities
     from their rank-nocc factors, FP64 pipe fraction, and the difference from the
@@ -300,9 +411,8 @@ def measure_cd(ltjk, torch, stream, ctx, w, D, J, K, Co, Cv, eo, ev, X, t, delta
     nd, r = V.shape[0], V.shape[2]
     # B U once; per density B V_q, sum_Q (B_Q U)(B_Q V_q)^T, gamma and J
     flops = 2.0 * naux * N * N * r + nd * (4.0 * naux * N * N * r + 2.0 * naux * N * r + 2.0 * naux * N * N)
-    pk = alu_peaks(2070.0)
     native = ctx.precision == ltjk.FP64_NATIVE
-    peak = pk["fp64_tflops"] if native else pk["fp32_tflops"] / 2.0 * 2.0 / 15.0
+    peak = peaks["fp64_fma_tflops"] if native else peaks["dfloat_fma_tflops"]
     dj = float((Jc - J).abs().max())
     dk = float((Kc - K).abs().max())
     bound = res * float(D.abs().sum(dim=(1, 2)).max())
@@ -422,63 +532,69 @@ def run_gpu(args, world, rank, local):
                "J_max_rel_to_max": dj / J64.abs().max().item(), "K_max_rel_to_max": dk / K64.abs().max().item(),
                "fp64_single_request_builds_per_s": nd / (fp64_ms / 1e3)}
         del c64
-    # roofline of the dominant kernel (the J/K quartet kernels of one build)
+    # roofline of the dominant kernel (the J/K quartet kernels of one build,
+    # 21 class launches, > 99 % of the step), against arithmetic peaks
+    # measured on this GPU in this run
     clocks = clk.summary(local)
+    peaks = measure_alu_peaks(ltjk, torch, stream)
     jk_s = statistics.mean(jk_ms) / 1e3
     dig = 20.0 * st["cart_integrals_kept"] * nd
-    flops = st["eri_flops_per_build"] + dig
-    flops64 = st["eri_flops_fp64"] + 20.0 * st["cart_integrals_fp64"] * nd
-    pk = alu_peaks(2070.0)
-    # FP64-class arithmetic as double-float on the FP32 pipe: one double-float
-    # FMA (2 flops) costs 15 FP32 instructions, so its peak is 2/15 of the FP32
-    # instruction rate; mixed precision weights the double-float and FP32 peaks
-    # by the share of algorithmic flops in each.
-    df_peak = pk["fp32_tflops"] / 2.0 * 2.0 / 15.0
+    dig64 = 20.0 * st["cart_integrals_fp64"] * nd
+    eri, eri64 = st["eri_flops_per_build"], st["eri_flops_fp64"]
+    flops = eri + dig
     if prec == ltjk.FP64_NATIVE:
-        peak, pipe = pk["fp64_tflops"], "fp64 FMA"
-        src = "152 SMs x 2 FP64 FMA/clk x 2070 MHz"
-    elif prec == ltjk.FP64:
-        peak, pipe = df_peak, "fp32 FMA pipe running double-float (15 FP32 instructions per FMA)"
-        src = "152 SMs x 128 FP32 lanes x 2070 MHz x 2 flops / 15 instructions"
+        parts = [(flops, peaks["fp64_fma_tflops"])]
+        pipe = "fp64 FMA pipe (IEEE binary64 throughout)"
     else:
-        f64 = flops64 / flops
-        peak = 1.0 / (f64 / df_peak + (1.0 - f64) / pk["fp32_tflops"])
-        pipe = f"fp32 FMA pipe: {100 * f64:.0f}% of the flops double-float, the rest FP32"
-        src = ("harmonic mix of the double-float peak (FP32 rate x 2/15) and the FP32 FMA peak "
-               "(152 x 128 x 2 x 2070 MHz) by flop share")
+        parts = [(eri64, peaks["dfloat_fma_tflops"]), (dig64, peaks["dfloat_dot_tflops"]),
+                 (eri - eri64, peaks["fp32_fma_tflops"]), (dig - dig64, peaks["fp32_fma_tflops"])]
+        pipe = (f"fp32 pipe: {100 * (eri64 + dig64) / flops:.0f}% of the flops double-float "
+                f"(recurrences as FMAs, digestion as dot-product accumulation), the rest binary32")
+    peak = mixed_peak(parts)
     roof = {"bound": "alu", "pipe": pipe,
             "achieved": flops / jk_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-            "frac": flops / jk_s / 1e12 / peak, "traffic": NCU_DRAM_BYTES_PER_BUILD[args.precision],
-            "traffic_unit": "bytes per build (all class launches of one build)",
+            "frac": flops / jk_s / 1e12 / peak, "traffic": None,
+            "traffic_note": ("not captured for this kernel version: the working set (density copies and "
+                             "accumulators, 56 nd N^2 bytes = 108 MB here) is L2-resident, so DRAM counts "
+                             "only first-touch traffic of an arithmetic-bound path"),
             "algorithmic_bytes_per_build": 3 * nd * N * N * 8,
-            "algorithmic_flops_per_build": flops, "peak_source": src,
-            "fp32_pipe_peak_tflops": pk["fp32_tflops"], "fp64_pipe_peak_tflops": pk["fp64_tflops"]}
+            "algorithmic_flops_per_build": flops,
+            "flops_split": {"eri_fp64_class": eri64, "digestion_fp64_class": dig64,
+                            "eri_fp32": eri - eri64, "digestion_fp32": dig - dig64},
+            "peak_source": ("harmonic mix by flop share of arithmetic peaks measured in this run "
+                            "(ltjk_alu_peak, CUDA events, best of 5); of measured"),
+            "measured_peaks_tflops": peaks,
+            "nominal_peaks_tflops": alu_peaks(2070.0, torch.cuda.get_device_properties(local).multi_processor_count)}
     extras = {}
     if not args.no_extras and rank == 0:
-        extras["next_rows"] = measure_next_rows(ltjk, torch, stream, ctx, w, J, K, Co, Cv, xmin, xmax)
+        extras["next_rows"] = measure_next_rows(ltjk, torch, stream, ctx, w, J, K, Co, Cv, xmin, xmax, peaks)
         tq, _, _ = ltjk.laplace_quadrature(xmin, xmax, w.nlap)
-        extras["next_rows"]["cholesky_jk"] = measure_cd(ltjk, torch, stream, ctx, w, D, J, K, Co, Cv, eo, ev, X, tq)
-        extras["gradient"] = measure_gradient(ltjk, torch, dev, local, stream, prec)
+        extras["next_rows"]["cholesky_jk"] = measure_cd(ltjk, torch, stream, ctx, w, D, J, K, Co, Cv, eo, ev, X, tq,
+                                                        peaks)
+        extras["gradient"] = measure_gradient(ltjk, torch, dev, local, stream, prec, peaks)
         extras["macrocycle_445"] = measure_macrocycle(ltjk, torch, dev, local, stream)
+        extras["water_fp64_single_request"] = measure_config1(ltjk, torch, dev, local, stream)
+        extras["serving"] = measure_serving(ltjk, torch, dev)
+        pc = extras["serving"]["paced"]
+        extras["latency"] = {"p50_ms": pc["p50_ms"], "p99_ms": pc["p99_ms"],
+                             "what": "serving stream, 0.8 x capacity, mixed precision (see serving.paced)"}
     if rank != 0:
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_oracle_sample(w, budget_s=args.cpu_seconds)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    cfg = bench_config(w, args.precision)
+    cfg.update({"laplace_max_rel_err": lap_err, "parallelism": f"replicas x{world}"})
     line = {
-        "metric": f"Laplace J/K builds/s ({args.precision}, 200-AO chain, 48 densities)",
+        "metric": METRIC,
         "value": value, "unit": "builds/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {ltjk.FP64_NATIVE: "f64", ltjk.FP64: "f64-class (f32 pairs + f64)",
                   ltjk.MIXED: "f32 + f64-class"}[prec],
         "data": "synthetic",
-        "config": {"workload": w.name, "precision": args.precision, "schwarz_tau": w.schwarz_tau,
-                   "mixed_tau": 1e-6 if prec == ltjk.MIXED else None, "nao": N, "ndens": nd,
-                   "laplace_points": w.nlap, "laplace_max_rel_err": lap_err,
-                   "l2": "flushed between timed steps (512 MB write)",
-                   "parallelism": f"replicas x{world}"},
+        "config": cfg,
         "quartets_per_s": world * st["quartets_kept"] * args.steps / total_s,
         "prim_quartets_per_s": world * st["prim_quartets_kept"] * args.steps / total_s,
         "jk_build_ms": statistics.mean(jk_ms),
@@ -504,9 +620,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp64-native"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-seconds", type=float, default=4.0,
+                    help="oracle seconds per timed step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the gradient and 445-AO macrocycle measurements")
+                    help="skip the measurements beside the headline (gradient, 445-AO macrocycle, "
+                         "next rows, 25-AO FP64 request, serving stream)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -99,14 +99,26 @@ typedef struct {
      mixed_tau    precision == LTJK_MIXED only: quartets with Q_ab*Q_cd > mixed_tau
                   are evaluated FP64-class, the rest in FP32 (Boys function always
                   FP64; J/K always accumulated in FP64).
-     precision    LTJK_FP64, LTJK_MIXED or LTJK_FP64_NATIVE.  The Boys function,
-                  the per-primitive setup and the accumulation across quartets
-                  are IEEE FP64 in every mode.  LTJK_FP64 runs the recurrences
-                  and the density digestion in double-float arithmetic (pairs of
-                  FP32 words, about 2^-44 relative per operation) on the FP32
-                  pipe, which on GB300 is 58x faster than its FP64 pipe;
-                  LTJK_FP64_NATIVE keeps them in IEEE FP64.  Both meet the FP64
-                  parity gate (1e-10 relative to the oracle).
+     precision    LTJK_FP64, LTJK_MIXED or LTJK_FP64_NATIVE.  LTJK_FP64 (FP64
+                  class) runs the Boys function, the per-primitive set-up, the
+                  recurrences and the density digestion in double-float
+                  arithmetic (pairs of FP32 words, about 2^-44 relative per
+                  operation) on the FP32 pipe, which on GB300 is 58x faster
+                  than its FP64 pipe; LTJK_FP64_NATIVE keeps every step in IEEE
+                  binary64.  Both meet the FP64 parity gate (1e-10 relative to
+                  the oracle).  LTJK_MIXED evaluates the quartets above
+                  mixed_tau as LTJK_FP64 and the rest with binary32
+                  recurrences and digestion (their Boys function and set-up in
+                  double-float, rounded to binary32).  The accumulation across
+                  quartets is IEEE binary64 in every mode.
+                  Range: each density is scaled by the exact power of two that
+                  brings its largest element into [1/2, 1) before the
+                  double-float and binary32 copies are made, and J and K are
+                  scaled back exactly, so D may take any binary64 magnitude
+                  (elements below 2^-126 of their density's largest element
+                  are flushed in the binary32 words of the FP64-class and
+                  mixed modes: an absolute error far below their 1e-10 and
+                  stated tolerances).
      device       CUDA device ordinal the context lives on. */
 typedef struct {
   double schwarz_tau;
@@ -131,6 +143,8 @@ typedef struct {
   size_t device_bytes;        /* device memory held by the context */
   double eri_flops_fp64;      /* part of eri_flops_per_build in FP64-class quartets */
   int64_t cart_integrals_fp64;/* part of cart_integrals_kept in FP64-class quartets */
+  double grad_eri_flops;      /* derivative-recurrence flop model over the kept quartets */
+  double grad_eri_flops_fp64; /* part of grad_eri_flops in FP64-class quartets */
 } ltjk_ctx_stats;
 
 /* Create a context: normalises the basis, builds every shell pair and its
@@ -226,9 +240,9 @@ int ltjk_jk_build(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *
    through their own pool or framework allocator, or latency-critical loops
    that cannot absorb the device-wide synchronisation of cudaMalloc/cudaFree.
    The paper has no counterpart; this is an interface convenience.
-     Limit: 4 * ndens * N * N doubles (FP64 contexts) or 5 * ndens * N * N
-     (mixed contexts) must not exceed 8 * 2^20; larger requests return
-     LTJK_EINVAL with the sizes in ltjk_last_error().
+     Limit: 4 * ndens * N * N + ndens doubles (FP64 contexts) or
+     5 * ndens * N * N + ndens (mixed contexts) must not exceed 8 * 2^20;
+     larger requests return LTJK_EINVAL with the sizes in ltjk_last_error().
      The first call on each device looks up the array's device address
      (cudaGetSymbolAddress) with that device current; make that first call
      before any stream capture.
@@ -239,6 +253,25 @@ int ltjk_jk_build(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *
    Arguments, layouts and results are those of ltjk_jk_build. */
 int ltjk_jk_build_noalloc(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *K,
                           ltjk_stream stream);
+
+/* F[q] = cJ J[D_q] + cK K[D_q]: the combination a gradient's adjoint with
+   respect to a density takes (Eq. jkderiv: dE/dP_r = cJ J[Q_r] + cK K[Q_r]
+   for E = sum_r [cJ J(P_r, Q_r) + cK K(P_r, Q_r)]), formed in the build's
+   epilogue.  D, F [ndens][N][N] device (F overwritten; D and F must not
+   overlap); 1 <= ndens <= 4096; a zero coefficient skips that build.  Uses
+   the context's scratch. */
+int ltjk_jk_fock(ltjk_ctx *ctx, int ndens, const double *D, double cJ, double cK, double *F,
+                 ltjk_stream stream);
+
+/* The energy functional of the gradient adjoint,
+     E = sum_r <P_r, cJ J[Q_r] + cK K[Q_r]> = sum_r [cJ J(P_r, Q_r) + cK K(P_r, Q_r)]
+   (Eq. jkderiv; <A, B> = sum_{mu nu} A_{mu nu} B_{mu nu}), with F = cJ J[Q] +
+   cK K[Q] from ltjk_jk_fock.  P, Q [nterms][N][N] device; F [nterms][N][N]
+   device (written, nullable: then kept in scratch); E one device double
+   (overwritten).  The sum over elements is taken in a fixed order (no
+   atomics), so E is reproducible for a given F.  1 <= nterms <= 4096. */
+int ltjk_jk_energy(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, double cJ,
+                   double cK, double *F, double *E, ltjk_stream stream);
 
 /* ---------------------------------------------------------- gradient adjoint */
 /* grad[A][x] = d/dR_{A,x} sum_r [cJ J(P_r, Q_r) + cK K(P_r, Q_r)] with the
@@ -262,6 +295,18 @@ int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, do
 int ltjk_laplace_fock(ltjk_ctx *ctx, int ndens, const double *J, const double *K, double cJ,
                       double cK, int nl, const double *C_left, int nr, const double *C_right,
                       double *F, ltjk_stream stream);
+
+/* ------------------------------------------------------- measurement */
+/* One launch of an arithmetic-throughput kernel on the caller's stream (the
+   roofline denominators of the benchmark; not part of the method): every
+   thread of a grid of 4 CTAs x 256 threads per SM runs 8 independent chains of
+   fused multiply-adds.  kind 0: binary32 FMA; 1: binary64 FMA; 2: double-float
+   FMA (the FP64-class arithmetic of the recurrences); 3: the double-float
+   dot-product accumulation of the density digestion.  *flops (host) receives
+   the algorithmic flops of one launch (2 per multiply-add); time the launch
+   with events on the stream.  The kernel's results go to a file-scope device
+   word (nothing is allocated). */
+int ltjk_alu_peak(int kind, double *flops, ltjk_stream stream);
 
 /* ------------------------------------------------------ spherical AOs */
 /* Matrix-level Cartesian <-> real-spherical transformation.  The paper works

@@ -369,7 +369,7 @@ int ltjk_cd_factor(ltjk_ctx *ctx, double delta, int max_vectors, double *B, int 
     if ((rc = store_blocks(c, qs, LTJK_FP64_NATIVE, offs, d_blocks.as<double>(), st))) return rc;
     if ((rc = d_off.upload(offs))) return rc;
     CUDA_TRY(cudaMemsetAsync(d_d.p, 0, NN * sizeof(double), st));
-    cd_diag_scatter<<<std::min(c.npairs, 152 * 8), 128, 0, st>>>(
+    cd_diag_scatter<<<std::min(c.npairs, num_sms() * 8), 128, 0, st>>>(
         d_blocks.as<double>(), d_off.as<long long>(), d_geo.as<int4>(), c.npairs, N, d_d.as<double>());
     CUDA_TRY(cudaGetLastError());
     g_launches += 1;
@@ -388,7 +388,7 @@ int ltjk_cd_factor(ltjk_ctx *ctx, double delta, int max_vectors, double *B, int 
   }
   int nvec = 0;
   double best = 0.0;
-  const int steps_grid = (int)std::min<size_t>((NN + 255) / 256, 152 * 16);
+  const int steps_grid = (int)std::min<size_t>((NN + 255) / 256, num_sms() * 16);
   for (;;) {
     cd_argmax<<<1, 1024, 0, st>>>(d_d.as<double>(), N, d_best.as<double>(),
                                   reinterpret_cast<int *>(d_best.as<double>() + 1));
@@ -411,7 +411,7 @@ int ltjk_cd_factor(ltjk_ctx *ctx, double delta, int max_vectors, double *B, int 
       if ((rc = d_off.upload(offs))) return rc;
       auto buf = std::make_unique<DevBuf>();
       if ((rc = buf->alloc((size_t)nst * NN * sizeof(double), st))) return rc;
-      cd_col_scatter<<<std::min(c.npairs, 152 * 8), 128, 0, st>>>(
+      cd_col_scatter<<<std::min(c.npairs, num_sms() * 8), 128, 0, st>>>(
           d_blocks.as<double>(), d_off.as<long long>(), d_geo.as<int4>(), c.npairs, N, nst, buf->as<double>());
       CUDA_TRY(cudaGetLastError());
       g_launches += 1;
@@ -451,13 +451,13 @@ int ltjk_pseudo_density_factors(ltjk_ctx *ctx, int nocc, int nvir, const double 
   double *Y = ctx->scratch.as<double>();
   CUDA_TRY(cudaMemcpyAsync(ctx->d_t.p, t_host, sizeof(double) * nlap, cudaMemcpyHostToDevice, st));
   // Y[q*npair+p][i][a] = exp(t_q (eps_i - eps_a)) X[p][i][a]   (Eq. scaledcoeff)
-  scale_amplitudes<<<(int)std::min<size_t>((ny + 255) / 256, 152 * 16), 256, 0, st>>>(
+  scale_amplitudes<<<(int)std::min<size_t>((ny + 255) / 256, num_sms() * 16), 256, 0, st>>>(
       X, eps_occ, eps_vir, ctx->d_t.as<double>(), Y, nlap, npair, nocc, nvir);
   // V[q] = C_vir Y[q]^T   ([N][nvir] x [nvir][nocc])
   const dim3 thr(16, 16), g((nocc + 15) / 16, (N + 15) / 16, nq);
   gemm_f64<true><<<g, thr, 0, st>>>(C_vir, 0, Y, (long long)nocc * nvir, V, (long long)nu, N, nocc, nvir, nvir,
                                     nvir, nocc);
-  cd_replicate<<<(int)std::min<size_t>((nu * nq + 255) / 256, 152 * 16), 256, 0, st>>>(C_occ, nu, nq, U);
+  cd_replicate<<<(int)std::min<size_t>((nu * nq + 255) / 256, num_sms() * 16), 256, 0, st>>>(C_occ, nu, nq, U);
   CUDA_TRY(cudaGetLastError());
   g_launches += 3;
   return LTJK_OK;
@@ -488,7 +488,7 @@ int ltjk_cd_jk(ltjk_ctx *ctx, int naux, const double *B, int ndens, int rank, in
     const long long M = (long long)naux * N;  // B viewed as [naux*N][N]
     const dim3 gbu((unsigned)((M + 15) / 16), (unsigned)((rank + 15) / 16));
     const int tiles = ((N + 15) / 16) * ((N + 15) / 16);
-    const int qsplit = std::max(1, std::min(naux, 152 * 8 / std::max(1, tiles) + 1));
+    const int qsplit = std::max(1, std::min(naux, num_sms() * 8 / std::max(1, tiles) + 1));
     const int qchunk = (naux + qsplit - 1) / qsplit;
     for (int q = 0; q < ndens; ++q) {
       const double *Uq = U + (size_t)q * u_stride, *Vq = V + (size_t)q * per;
@@ -497,7 +497,7 @@ int ltjk_cd_jk(ltjk_ctx *ctx, int naux, const double *B, int ndens, int rank, in
         g_launches += 1;
       }
       cd_gemm<false><<<gbu, thr, 0, st>>>(B, Vq, BV, M, rank, N, N, rank, rank);
-      cd_gamma<<<std::min(naux, 152 * 8), 256, 0, st>>>(BU, Vq, naux, per, gamma + (size_t)q * naux);
+      cd_gamma<<<std::min(naux, num_sms() * 8), 256, 0, st>>>(BU, Vq, naux, per, gamma + (size_t)q * naux);
       g_launches += 2;
       if (K) {
         double *Kq = K + (size_t)q * NN;
@@ -522,7 +522,7 @@ int ltjk_cd_jk(ltjk_ctx *ctx, int naux, const double *B, int ndens, int rank, in
     const long long M = (long long)naux * N;
     const long long kd = (long long)naux * rank;
     const int ktiles = ((N + 63) / 64) * ((N + 63) / 64);
-    const int zsplit = (int)std::max<long long>(1, std::min<long long>((kd + 15) / 16, (152 * 3 + ktiles - 1) / ktiles));
+    const int zsplit = (int)std::max<long long>(1, std::min<long long>((kd + 15) / 16, (num_sms() * 3 + ktiles - 1) / ktiles));
     const long long kchunk = ((kd + zsplit - 1) / zsplit + 15) / 16 * 16;
     const int gz = (int)((kd + kchunk - 1) / kchunk);
     for (int q0 = 0; q0 < ndens; q0 += chunk) {
@@ -531,17 +531,17 @@ int ltjk_cd_jk(ltjk_ctx *ctx, int naux, const double *B, int ndens, int rank, in
       if (q0 == 0 || u_stride) {
         const int nu = u_stride ? nc : 1;
         const double *Uq = U + (size_t)q0 * u_stride;
-        cd_transpose_factors<<<(int)std::min<size_t>((per * nu + 255) / 256, 152 * 16), 256, 0, st>>>(
+        cd_transpose_factors<<<(int)std::min<size_t>((per * nu + 255) / 256, num_sms() * 16), 256, 0, st>>>(
             Uq, nu, N, rank, Ut);
         cd_gemm_nt_df<kEpiPerm><<<dim3((unsigned)((M + 63) / 64), (unsigned)((nu * rank + 63) / 64), 1), 256, 0,
                                   st>>>(B, N, Ut, N, BU, 0, M, nu * rank, N, N, ps);
         g_launches += 2;
       }
-      cd_transpose_factors<<<(int)std::min<size_t>((per * nc + 255) / 256, 152 * 16), 256, 0, st>>>(
+      cd_transpose_factors<<<(int)std::min<size_t>((per * nc + 255) / 256, num_sms() * 16), 256, 0, st>>>(
           V + (size_t)q0 * per, nc, N, rank, Vt);
       cd_gemm_nt_df<kEpiPerm><<<dim3((unsigned)((M + 63) / 64), (unsigned)((nc * rank + 63) / 64), 1), 256, 0,
                                 st>>>(B, N, Vt, N, BV, 0, M, nc * rank, N, N, ps);
-      cd_gamma_perm<<<(int)std::min<long long>(((long long)nc * naux * 32 + 255) / 256, 152 * 32), 256, 0, st>>>(
+      cd_gamma_perm<<<(int)std::min<long long>(((long long)nc * naux * 32 + 255) / 256, num_sms() * 32), 256, 0, st>>>(
           BU, u_stride ? blk : 0, V + (size_t)q0 * per, nc, naux, N, rank, gamma + (size_t)q0 * naux);
       g_launches += 3;
       if (K && !u_stride) {
@@ -550,7 +550,7 @@ int ltjk_cd_jk(ltjk_ctx *ctx, int naux, const double *B, int ndens, int rank, in
         CUDA_TRY(cudaMemsetAsync(K + (size_t)q0 * NN, 0, (size_t)nc * NN * sizeof(double), st));
         const int ctiles = (nc * N + 63) / 64, rtiles = (N + 63) / 64;
         const int zk = (int)std::max<long long>(1, std::min<long long>((kd + 15) / 16,
-                                                                        (152 * 3 + rtiles * ctiles - 1) / (rtiles * ctiles)));
+                                                                        (num_sms() * 3 + rtiles * ctiles - 1) / (rtiles * ctiles)));
         const long long kchunk_c = ((kd + zk - 1) / zk + 15) / 16 * 16;
         const int gzc = (int)((kd + kchunk_c - 1) / kchunk_c);
         cd_gemm_nt_df<kEpiAtomicK><<<dim3(rtiles, ctiles, gzc), 256, 0, st>>>(

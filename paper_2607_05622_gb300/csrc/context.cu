@@ -254,7 +254,7 @@ int launch_class(const DevProgs &PR, const ClassLaunch &cl_in, const JobTable &T
     return set_error(LTJK_EUNSUPPORTED, "class (%d%d|%d%d) needs %zu bytes of shared memory",
                      cl.p.la, cl.p.lb, cl.p.lc, cl.p.ld, smem);
   const int ctas_needed = (T.total + cl.warps - 1) / cl.warps;
-  const int grid = std::min(ctas_needed, 152 * 32);
+  const int grid = std::min(ctas_needed, num_sms() * 32);
   quartet_kernel<Real, MODE><<<grid, 32 * cl.warps, smem, st>>>(PR, cl, T);
   CUDA_TRY(cudaGetLastError());
   g_launches += 1;
@@ -502,9 +502,12 @@ int store_blocks(ltjk_ctx &c, const std::vector<std::pair<int, int>> &qs, int pr
 }
 
 // Flop model of a class (per contracted quartet with npq primitive quartets).
-double class_flops(const ClassProg &p, long long npq) {
+// (npq primitive quartets over nq contracted quartets): per primitive quartet
+// the vertical recurrence, the Boys function and set-up, the accumulation;
+// per contracted quartet the horizontal recurrence.
+double class_flops(const ClassProg &p, long long npq, long long nq) {
   const double boys = 40.0;
-  return npq * (p.vrr_flops + boys + 30.0 + 2.0 * p.nacc) + p.hrr_flops;
+  return npq * (p.vrr_flops + boys + 30.0 + 2.0 * p.nacc) + nq * p.hrr_flops;
 }
 
 int build_work(ltjk_ctx &c) {
@@ -524,6 +527,8 @@ int build_work(ltjk_ctx &c) {
   c.stats.eri_flops_per_build = 0;
   c.stats.eri_flops_fp64 = 0;
   c.stats.cart_integrals_fp64 = 0;
+  c.stats.grad_eri_flops = 0;
+  c.stats.grad_eri_flops_fp64 = 0;
   std::vector<int> npp_host(c.npairs);
   {
     // primitive pair counts are needed for the statistics
@@ -546,6 +551,7 @@ int build_work(ltjk_ctx &c) {
       cw->ld = c.sh_l[t0.y];
       cw->ket_base = yb;
       const ClassProg &p = ps->progs[quartet_index(cw->la, cw->lb, cw->lc, cw->ld, 0)];
+      const ClassProg &pd = ps->progs[quartet_index(cw->la, cw->lb, cw->lc, cw->ld, 1)];
       // Schwarz-kept ket prefix of every bra pair, split FP64-class / FP32
       std::vector<int> keep(xe - xb), n64v(xe - xb);
       long long tot64 = 0, tot32 = 0;
@@ -586,8 +592,10 @@ int build_work(ltjk_ctx &c) {
         const long long nint = (long long)ncart(cw->la) * ncart(cw->lb) * ncart(cw->lc) * ncart(cw->ld);
         c.stats.cart_integrals_kept += (long long)nkeep * nint;
         c.stats.cart_integrals_fp64 += (long long)n64 * nint;
-        c.stats.eri_flops_per_build += class_flops(p, npq);
-        if (n64 > 0) c.stats.eri_flops_fp64 += class_flops(p, npq64);
+        c.stats.eri_flops_per_build += class_flops(p, npq, nkeep);
+        c.stats.eri_flops_fp64 += class_flops(p, npq64, n64);
+        c.stats.grad_eri_flops += class_flops(pd, npq, nkeep);
+        c.stats.grad_eri_flops_fp64 += class_flops(pd, npq64, n64);
       }
       // kets per work item: small enough that a class yields at least
       // kTargetItems items (heavy classes have few quartets), at most kKetChunk
@@ -613,22 +621,30 @@ int build_work(ltjk_ctx &c) {
 
 
 // Device scratch of one J/K build of nd densities: two density copies, the J
-// and K accumulators (q-innermost), plus FP32 copies in mixed precision.
+// and K accumulators (q-innermost), plus FP32 copies in mixed precision, plus
+// one power-of-two scale per density.
 size_t jk_scratch_bytes(const ltjk_ctx *c, int nd) {
   const size_t n = (size_t)c->nao * c->nao * nd;
-  return 4 * n * sizeof(double) + (c->opts.precision == LTJK_MIXED ? 2 * n * sizeof(float) : 0);
+  return 4 * n * sizeof(double) + (c->opts.precision == LTJK_MIXED ? 2 * n * sizeof(float) : 0) +
+         (size_t)nd * sizeof(double);
 }
 
-// Enqueue the layout transposes and the accumulator clear of one J/K build
-// whose scratch starts at `base`; returns the kernel arguments.
-JKArgs jk_prologue(const ltjk_ctx *c, const double *D, void *base, int nd, bool wantJ, bool wantK,
-                   cudaStream_t st) {
+// Enqueue the per-density scales, the layout transposes and the accumulator
+// clear of one J/K build whose scratch starts at `base` (jk_scratch_bytes
+// bytes); the kernel arguments go to *out.  Each density is scaled by the
+// power of two that brings its largest element into [1/2, 1): the build is
+// linear in D and the scaling is exact, so the double-float and binary32
+// copies keep their full relative precision whatever the magnitude of D
+// (binary32 words alone would flush elements below 2^-126 to zero).
+int jk_prologue(const ltjk_ctx *c, const double *D, void *base, int nd, bool wantJ, bool wantK,
+                cudaStream_t st, JKArgs *out) {
   const size_t n = (size_t)c->nao * c->nao * nd;
   double *A = static_cast<double *>(base), *Bq = A + n, *Jq = Bq + n, *Kq = Jq + n;
   const bool native = c->opts.precision == LTJK_FP64_NATIVE;
   const bool mixed = c->opts.precision == LTJK_MIXED;
   float *D32 = mixed ? reinterpret_cast<float *>(Kq + n) : nullptr;
   float *S32 = mixed ? D32 + n : nullptr;
+  double *scale = Kq + n + (mixed ? n : 0);
   JKArgs a{};
   if (native) {
     a.D = A;
@@ -642,13 +658,28 @@ JKArgs jk_prologue(const ltjk_ctx *c, const double *D, void *base, int nd, bool 
   a.J = wantJ ? Jq : nullptr;
   a.K = wantK ? Kq : nullptr;
   a.nd = nd;
-  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  a.scale = scale;
+  density_scales<<<nd, 256, 0, st>>>(D, (size_t)c->nao * c->nao, scale);
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16);
   to_qinner<<<blocks, 256, 0, st>>>(D, native ? A : nullptr, native ? Bq : nullptr, D32, S32, nd,
                                     c->nao, native ? nullptr : reinterpret_cast<dflt *>(A),
-                                    native ? nullptr : reinterpret_cast<dflt *>(Bq));
+                                    native ? nullptr : reinterpret_cast<dflt *>(Bq), scale);
+  CUDA_TRY(cudaGetLastError());
+  g_launches += 2;
+  CUDA_TRY(cudaMemsetAsync(Jq, 0, 2 * n * sizeof(double), st));
+  *out = a;
+  return LTJK_OK;
+}
+
+// Enqueue the epilogue of one J/K build: J = Jh + Jh^T and K, unscaled, in
+// the caller's [nd][N][N] layout.
+int jk_epilogue(const ltjk_ctx *c, const JKArgs &a, double *J, double *K, cudaStream_t st) {
+  const size_t n = (size_t)c->nao * c->nao * a.nd;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16);
+  from_qinner<<<blocks, 256, 0, st>>>(a.J, a.K, J, K, a.nd, c->nao, a.scale);
+  CUDA_TRY(cudaGetLastError());
   g_launches += 1;
-  cudaMemsetAsync(Jq, 0, 2 * n * sizeof(double), st);
-  return a;
+  return LTJK_OK;
 }
 
 // The class launches of one pass (J/K or gradient) over a context's work
@@ -989,16 +1020,66 @@ int ltjk_jk_build(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *
   if (!J && !K) return LTJK_OK;
   CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const size_t n = (size_t)ctx->nao * ctx->nao * ndens;
   int rc = ctx->ensure_scratch(jk_scratch_bytes(ctx, ndens), st);
   if (rc) return rc;
-  const JKArgs a = jk_prologue(ctx, D, ctx->scratch.p, ndens, J != nullptr, K != nullptr, st);
-  CUDA_TRY(cudaGetLastError());
+  JKArgs a;
+  if ((rc = jk_prologue(ctx, D, ctx->scratch.p, ndens, J != nullptr, K != nullptr, st, &a))) return rc;
   if ((rc = launch_classes<kJK>(ctx, a, st))) return rc;
-  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-  from_qinner<<<blocks, 256, 0, st>>>(a.J, a.K, J, K, ndens, ctx->nao);
+  return jk_epilogue(ctx, a, J, K, st);
+}
+
+// F = cJ J[D] + cK K[D] into F ([ndens][N][N], device), scratch at `base`
+// (jk_scratch_bytes bytes).
+static int jk_fock_into(ltjk_ctx *ctx, int ndens, const double *D, double cJ, double cK, double *F,
+                        void *base, cudaStream_t st) {
+  const size_t n = (size_t)ctx->nao * ctx->nao * ndens;
+  if (cJ == 0.0 && cK == 0.0) {
+    CUDA_TRY(cudaMemsetAsync(F, 0, n * sizeof(double), st));
+    return LTJK_OK;
+  }
+  JKArgs a;
+  int rc;
+  if ((rc = jk_prologue(ctx, D, base, ndens, cJ != 0.0, cK != 0.0, st, &a))) return rc;
+  if ((rc = launch_classes<kJK>(ctx, a, st))) return rc;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16);
+  from_qinner_fock<<<blocks, 256, 0, st>>>(a.J, a.K, F, ndens, ctx->nao, a.scale, cJ, cK);
   CUDA_TRY(cudaGetLastError());
   g_launches += 1;
+  return LTJK_OK;
+}
+
+int ltjk_jk_fock(ltjk_ctx *ctx, int ndens, const double *D, double cJ, double cK, double *F,
+                 ltjk_stream stream) {
+  if (!ctx || !D || !F) return set_error(LTJK_EINVAL, "jk_fock: null argument");
+  if (ndens < 1 || ndens > 4096) return set_error(LTJK_EINVAL, "jk_fock: ndens %d not in 1..4096", ndens);
+  if (!std::isfinite(cJ) || !std::isfinite(cK)) return set_error(LTJK_EINVAL, "jk_fock: non-finite coefficient");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int rc = ctx->ensure_scratch(jk_scratch_bytes(ctx, ndens), st);
+  if (rc) return rc;
+  return jk_fock_into(ctx, ndens, D, cJ, cK, F, ctx->scratch.p, st);
+}
+
+int ltjk_jk_energy(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, double cJ,
+                   double cK, double *F, double *E, ltjk_stream stream) {
+  if (!ctx || !P || !Q || !E) return set_error(LTJK_EINVAL, "jk_energy: null argument");
+  if (nterms < 1 || nterms > 4096) return set_error(LTJK_EINVAL, "jk_energy: nterms %d not in 1..4096", nterms);
+  if (!std::isfinite(cJ) || !std::isfinite(cK)) return set_error(LTJK_EINVAL, "jk_energy: non-finite coefficient");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = (size_t)ctx->nao * ctx->nao * nterms;
+  const int nb = (int)std::min<size_t>((n + 4095) / 4096, 1024);
+  const size_t jk = (jk_scratch_bytes(ctx, nterms) + 255) / 256 * 256;
+  int rc = ctx->ensure_scratch(jk + (F ? 0 : n * sizeof(double)) + nb * sizeof(double), st);
+  if (rc) return rc;
+  char *base = static_cast<char *>(ctx->scratch.p);
+  double *Fb = F ? F : reinterpret_cast<double *>(base + jk);
+  double *partial = reinterpret_cast<double *>(base + jk + (F ? 0 : n * sizeof(double)));
+  if ((rc = jk_fock_into(ctx, nterms, Q, cJ, cK, Fb, base, st))) return rc;
+  dot_partial<<<nb, 256, 0, st>>>(P, Fb, n, partial);
+  dot_final<<<1, 32, 0, st>>>(partial, nb, E);
+  CUDA_TRY(cudaGetLastError());
+  g_launches += 2;
   return LTJK_OK;
 }
 
@@ -1012,7 +1093,7 @@ int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, do
   int rc = ctx->ensure_scratch(2 * n * sizeof(double), st);
   if (rc) return rc;
   double *Pq = ctx->scratch.as<double>(), *Qq = Pq + n;
-  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16);
   to_qinner<<<blocks, 256, 0, st>>>(P, Pq, nullptr, nullptr, nullptr, nterms, ctx->nao);
   to_qinner<<<blocks, 256, 0, st>>>(Q, Qq, nullptr, nullptr, nullptr, nterms, ctx->nao);
   CUDA_TRY(cudaGetLastError());
@@ -1047,7 +1128,7 @@ int ltjk_pseudo_densities(ltjk_ctx *ctx, int nocc, int nvir, const double *C_occ
   if ((rc = ctx->ensure_scratch((ny + nz) * sizeof(double), st))) return rc;
   double *Y = ctx->scratch.as<double>(), *Z = Y + ny;
   CUDA_TRY(cudaMemcpyAsync(ctx->d_t.p, t_host, sizeof(double) * nlap, cudaMemcpyHostToDevice, st));
-  scale_amplitudes<<<(int)std::min<size_t>((ny + 255) / 256, 152 * 16), 256, 0, st>>>(
+  scale_amplitudes<<<(int)std::min<size_t>((ny + 255) / 256, (size_t)num_sms() * 16), 256, 0, st>>>(
       X, eps_occ, eps_vir, ctx->d_t.as<double>(), Y, nlap, npair, nocc, nvir);
   dim3 thr(16, 16);
   dim3 g1((N + 15) / 16, (nocc + 15) / 16, nq);
@@ -1075,7 +1156,7 @@ int ltjk_laplace_fock(ltjk_ctx *ctx, int ndens, const double *J, const double *K
   int rc = ctx->ensure_scratch((nm + nt) * sizeof(double), st);
   if (rc) return rc;
   double *M = ctx->scratch.as<double>(), *T = M + nm;
-  combine_jk<<<(int)std::min<size_t>((nm + 255) / 256, 152 * 16), 256, 0, st>>>(J, K, cJ, cK, M, nm);
+  combine_jk<<<(int)std::min<size_t>((nm + 255) / 256, (size_t)num_sms() * 16), 256, 0, st>>>(J, K, cJ, cK, M, nm);
   dim3 thr(16, 16);
   // T[q] = M[q] C_right            ([N][N] x [N][nr])
   gemm_f64<false><<<dim3((nr + 15) / 16, (N + 15) / 16, ndens), thr, 0, st>>>(
@@ -1109,6 +1190,23 @@ int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int preci
   }
   std::vector<long long> offs;
   return store_blocks(*ctx, qs, precision, offs, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int ltjk_alu_peak(int kind, double *flops, ltjk_stream stream) {
+  if (!flops || kind < 0 || kind > 3) return set_error(LTJK_EINVAL, "alu_peak: kind must be 0..3");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int blocks = num_sms() * 4, threads = 256;
+  const int iters = kind == 0 ? 16384 : kind == 1 ? 256 : 2048;
+  switch (kind) {
+    case 0: alu_peak_kernel<0><<<blocks, threads, 0, st>>>(iters, 0.999f, 1e-3f); break;
+    case 1: alu_peak_kernel<1><<<blocks, threads, 0, st>>>(iters, 0.999f, 1e-3f); break;
+    case 2: alu_peak_kernel<2><<<blocks, threads, 0, st>>>(iters, 0.999f, 1e-3f); break;
+    default: alu_peak_kernel<3><<<blocks, threads, 0, st>>>(iters, 0.999f, 1e-3f); break;
+  }
+  CUDA_TRY(cudaGetLastError());
+  g_launches += 1;
+  *flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+  return LTJK_OK;
 }
 
 int ltjk_class_program(int la, int lb, int lc, int ld, int deriv, ltjk_program_info *out) {
@@ -1185,8 +1283,7 @@ extern "C" int ltjk_jk_build_noalloc(ltjk_ctx *ctx, int ndens, const double *D, 
   if (ndens < 1 || ndens > 4096)
     return set_error(LTJK_EINVAL, "jk_build_noalloc: ndens %d not in 1..4096", ndens);
   if (!J && !K) return LTJK_OK;
-  const size_t n = (size_t)ctx->nao * ctx->nao * ndens;
-  const size_t need = jk_scratch_bytes(ctx, ndens) / sizeof(double);  // 4 (or 5) n doubles
+  const size_t need = jk_scratch_bytes(ctx, ndens) / sizeof(double);  // 4 (or 5) n + ndens doubles
   if (need > kNoallocDoubles)
     return set_error(LTJK_EINVAL,
                      "jk_build_noalloc: %d densities of %d AOs need %zu bytes of scratch, above the "
@@ -1198,14 +1295,10 @@ extern "C" int ltjk_jk_build_noalloc(ltjk_ctx *ctx, int ndens, const double *D, 
   if (rc) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   // the array keeps the previous call's contents; the prologue clears the accumulators
-  const JKArgs a = jk_prologue(ctx, D, base, ndens, J != nullptr, K != nullptr, st);
-  CUDA_TRY(cudaGetLastError());
+  JKArgs a;
+  if ((rc = jk_prologue(ctx, D, base, ndens, J != nullptr, K != nullptr, st, &a))) return rc;
   if ((rc = launch_classes<kJK>(ctx, a, st))) return rc;
-  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-  from_qinner<<<blocks, 256, 0, st>>>(a.J, a.K, J, K, ndens, ctx->nao);
-  CUDA_TRY(cudaGetLastError());
-  g_launches += 1;
-  return LTJK_OK;
+  return jk_epilogue(ctx, a, J, K, st);
 }
 
 #include "cholesky.cuh"

@@ -184,6 +184,7 @@ struct JKArgs {
   const dflt *S2;
   double *J;         // half-Coulomb accumulator (symmetrised afterwards)
   double *K;
+  const double *scale;  // per density: the power of two the copies were scaled by
   int nd;
   // store mode
   double *out;
@@ -702,20 +703,50 @@ __global__ void __launch_bounds__(128, 4) quartet_kernel(DevProgs PR, ClassLaunc
 }
 
 // --------------------------------------------------------- layout kernels
-// [nd][N][N] -> q-innermost [(mu*N+nu)*nd + q] copies of D and of S = D + D^T:
-// FP64 (Dq, Sq), double-float pairs (D2, S2) and FP32 (D32, S32); null = skip.
+// scale[q] = 2^-e with max_ij |D[q][i][j]| in [2^(e-1), 2^e): one block per
+// density.  A zero or non-finite maximum gives scale 1 (so NaN and Inf still
+// propagate to J and K).
+__global__ void density_scales(const double *__restrict__ D, size_t NN, double *__restrict__ scale) {
+  __shared__ double red[32];
+  const double *Dq = D + (size_t)blockIdx.x * NN;
+  double m = 0.0;
+  for (size_t t = threadIdx.x; t < NN; t += blockDim.x) m = fmax(m, fabs(Dq[t]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) {
+      // the exponent field of m gives e exactly: m = f 2^e with f in [1/2, 1)
+      const long long b = __double_as_longlong(m);
+      const int E = (int)((b >> 52) & 0x7FF);
+      double s = 1.0;
+      if (m > 0.0 && E > 0 && E < 0x7FF) {
+        const int e = E - 1022;
+        s = ldexp(1.0, -e);
+      }
+      scale[blockIdx.x] = s;
+    }
+  }
+}
+
+// [nd][N][N] -> q-innermost [(mu*N+nu)*nd + q] copies of s_q D and of
+// s_q (D + D^T) (s_q = scale[q], 1 when scale is null): FP64 (Dq, Sq),
+// double-float pairs (D2, S2) and FP32 (D32, S32); null = skip.
 __global__ void to_qinner(const double *__restrict__ D, double *__restrict__ Dq,
                           double *__restrict__ Sq, float *__restrict__ Dq32,
                           float *__restrict__ Sq32, int nd, int N, dflt *__restrict__ D2 = nullptr,
-                          dflt *__restrict__ S2 = nullptr) {
+                          dflt *__restrict__ S2 = nullptr, const double *__restrict__ scale = nullptr) {
   const size_t NN = (size_t)N * N;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < NN * nd;
        t += (size_t)gridDim.x * blockDim.x) {
     const int q = (int)(t % nd);
     const size_t mn = t / nd;
     const int mu = (int)(mn / N), nu = (int)(mn % N);
-    const double v = D[q * NN + mn];
-    const double sv = v + D[q * NN + (size_t)nu * N + mu];
+    const double s = scale ? scale[q] : 1.0;
+    const double v = D[q * NN + mn] * s;
+    const double sv = v + D[q * NN + (size_t)nu * N + mu] * s;
     if (Dq) Dq[t] = v;
     if (Sq) Sq[t] = sv;
     if (Dq32) Dq32[t] = (float)v;
@@ -725,17 +756,124 @@ __global__ void to_qinner(const double *__restrict__ D, double *__restrict__ Dq,
   }
 }
 
-// J[q] = Jh[q] + Jh[q]^T and K[q] from the q-innermost accumulators.
+// J[q] = (Jh[q] + Jh[q]^T) / s_q and K[q] = Kq[q] / s_q from the q-innermost
+// accumulators (s_q = scale[q], 1 when scale is null; dividing by a power of
+// two is exact).
 __global__ void from_qinner(const double *__restrict__ Jq, const double *__restrict__ Kq,
-                            double *__restrict__ J, double *__restrict__ K, int nd, int N) {
+                            double *__restrict__ J, double *__restrict__ K, int nd, int N,
+                            const double *__restrict__ scale = nullptr) {
   const size_t NN = (size_t)N * N;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < NN * nd;
        t += (size_t)gridDim.x * blockDim.x) {
     const int q = (int)(t / NN);
     const size_t mn = t % NN;
     const int mu = (int)(mn / N), nu = (int)(mn % N);
-    if (J) J[t] = Jq[mn * nd + q] + Jq[((size_t)nu * N + mu) * nd + q];
-    if (K) K[t] = Kq[mn * nd + q];
+    const double inv = scale ? 1.0 / scale[q] : 1.0;
+    if (J) J[t] = (Jq[mn * nd + q] + Jq[((size_t)nu * N + mu) * nd + q]) * inv;
+    if (K) K[t] = Kq[mn * nd + q] * inv;
+  }
+}
+
+// F[q] = (cJ (Jh[q] + Jh[q]^T) + cK Kq[q]) / s_q from the q-innermost
+// accumulators (a null accumulator contributes nothing).
+__global__ void from_qinner_fock(const double *__restrict__ Jq, const double *__restrict__ Kq,
+                                 double *__restrict__ F, int nd, int N, const double *__restrict__ scale,
+                                 double cJ, double cK) {
+  const size_t NN = (size_t)N * N;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < NN * nd;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t / NN);
+    const size_t mn = t % NN;
+    const int mu = (int)(mn / N), nu = (int)(mn % N);
+    double v = 0.0;
+    if (Jq) v = cJ * (Jq[mn * nd + q] + Jq[((size_t)nu * N + mu) * nd + q]);
+    if (Kq) v = fma(cK, Kq[mn * nd + q], v);
+    F[t] = v / scale[q];
+  }
+}
+
+// Deterministic dot product <P, F> over n elements: block b sums its
+// contiguous chunk in a fixed order into partial[b]; dot_final adds the
+// partials in index order.
+__global__ void dot_partial(const double *__restrict__ P, const double *__restrict__ F, size_t n,
+                            double *__restrict__ partial) {
+  __shared__ double red[32];
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+  double v = 0.0;
+  for (size_t t = b0 + threadIdx.x; t < b1; t += blockDim.x) v = fma(P[t], F[t], v);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = v;
+  }
+}
+__global__ void dot_final(const double *__restrict__ partial, int nb, double *__restrict__ E) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double v = 0.0;
+    for (int b = 0; b < nb; ++b) v += partial[b];
+    *E = v;
+  }
+}
+
+// --------------------------------------------------- arithmetic throughput
+// Eight independent multiply-add chains per thread, `iters` steps each; the
+// operands come from the launch so nothing folds, and the chains' sum is
+// stored only when it matches an impossible value, so nothing is dead.
+__device__ double g_alu_sink;
+template <int KIND>
+__global__ void __launch_bounds__(256) alu_peak_kernel(int iters, float b, float c) {
+  const float t = (float)(threadIdx.x + 1) * 1e-7f;
+  if (KIND == 0) {
+    float x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = t + k;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = fmaf(x[k], b, c);
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == -1.2345f) g_alu_sink = s;
+  } else if (KIND == 1) {
+    double x[8];
+    const double bd = b, cd = c;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = t + k;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = ::fma(x[k], bd, cd);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == -1.2345) g_alu_sink = s;
+  } else if (KIND == 2) {
+    dflt x[8];
+    const dflt bd(b, b * 1e-9f), cd(c, c * 1e-9f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = dflt(t + k, 0.0f);
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = fma(x[k], bd, cd);
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k].hi + x[k].lo;
+    if (s == -1.2345f) g_alu_sink = s;
+  } else {
+    DotAcc x[8];
+    const dflt bd(b, b * 1e-9f), cd(c, c * 1e-9f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = DotAcc{t + k, 0.0f};
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = acc_fma(x[k], bd, cd);
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k].hi + x[k].lo;
+    if (s == -1.2345f) g_alu_sink = s;
   }
 }
 

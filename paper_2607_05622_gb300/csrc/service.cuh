@@ -11,47 +11,9 @@
 #include <deque>
 #include <thread>
 
-namespace {
+#include "arena.h"
 
-// First-fit allocator over one device slab; freed blocks merge with neighbours.
-struct Arena {
-  char *base = nullptr;
-  size_t size = 0, used = 0, peak = 0;
-  std::map<size_t, size_t> free_;  // offset -> length
-  static constexpr size_t kAlign = 256;
-  bool alloc(size_t n, size_t *off) {
-    n = (n + kAlign - 1) / kAlign * kAlign;
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= n) {
-        *off = it->first;
-        const size_t rest = it->second - n, o = it->first;
-        free_.erase(it);
-        if (rest) free_[o + n] = rest;
-        used += n;
-        peak = std::max(peak, used);
-        return true;
-      }
-    }
-    return false;
-  }
-  void release(size_t off, size_t n) {
-    n = (n + kAlign - 1) / kAlign * kAlign;
-    used -= n;
-    auto it = free_.emplace(off, n).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-};
+namespace {
 
 enum JobState { kQueued = 0, kActive, kDraining, kDone, kCancelled, kFailed };
 
@@ -68,6 +30,7 @@ struct SvcJob {
   double t_submit = 0, t_done = 0;
   JKArgs a{};
   double *Jq = nullptr, *Kq = nullptr;
+  const double *scale = nullptr;  // per-density scales of the prologue
 };
 
 double now_s() {
@@ -120,7 +83,8 @@ namespace {
 
 size_t job_bytes(const ltjk_request &r, int nao, bool mixed) {
   const size_t n = (size_t)nao * nao * r.n;
-  if (r.kind == LTJK_REQ_JK) return 4 * n * sizeof(double) + (mixed ? 2 * n * sizeof(float) : 0);  // = jk_scratch_bytes
+  if (r.kind == LTJK_REQ_JK)  // = jk_scratch_bytes
+    return 4 * n * sizeof(double) + (mixed ? 2 * n * sizeof(float) : 0) + (size_t)r.n * sizeof(double);
   return 2 * n * sizeof(double);
 }
 
@@ -252,15 +216,17 @@ void ltjk_service::run() {
       ltjk_ctx *c = j->req.ctx;
       const size_t NN = (size_t)c->nao * c->nao, n = NN * j->req.n;
       double *mem = reinterpret_cast<double *>(arena.base + j->off);
-      const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+      const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16);
       j->cur64.assign(c->work.size(), 0);
       j->cur32.assign(c->work.size(), 0);
       JKArgs a{};
       if (j->req.kind == LTJK_REQ_JK) {
-        a = jk_prologue(c, j->req.D, mem, j->req.n, j->req.J != nullptr, j->req.K != nullptr, st);
+        if (jk_prologue(c, j->req.D, mem, j->req.n, j->req.J != nullptr, j->req.K != nullptr, st, &a) != LTJK_OK)
+          j->status = LTJK_ECUDA;
         j->Jq = mem + 2 * n;
         j->Kq = mem + 3 * n;
-        launches -= 1;  // counted below with the others
+        j->scale = a.scale;
+        g_launches -= 2;  // counted below with the others
       } else {
         double *Pq = mem, *Qq = Pq + n;
         to_qinner<<<blocks, 256, 0, st>>>(j->req.P, Pq, nullptr, nullptr, nullptr, j->req.n, c->nao);
@@ -309,8 +275,8 @@ void ltjk_service::run() {
       if (!j->cancel_req && j->req.kind == LTJK_REQ_JK) {
         ltjk_ctx *c = j->req.ctx;
         const size_t n = (size_t)c->nao * c->nao * j->req.n;
-        const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-        from_qinner<<<blocks, 256, 0, st>>>(j->Jq, j->Kq, j->req.J, j->req.K, j->req.n, c->nao);
+        const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16);
+        from_qinner<<<blocks, 256, 0, st>>>(j->Jq, j->Kq, j->req.J, j->req.K, j->req.n, c->nao, j->scale);
         g_launches += 1;
         launches += 1;
       }
@@ -386,9 +352,7 @@ int ltjk_service_create(size_t hbm_budget_bytes, int device, ltjk_service **out)
   void *p = nullptr;
   cudaError_t e = cudaMalloc(&p, hbm_budget_bytes);
   if (e != cudaSuccess) return set_error(LTJK_ENOMEM, "service arena of %zu bytes: %s", hbm_budget_bytes, cudaGetErrorString(e));
-  s->arena.base = static_cast<char *>(p);
-  s->arena.size = hbm_budget_bytes;
-  s->arena.free_[0] = hbm_budget_bytes;
+  s->arena.init(static_cast<char *>(p), hbm_budget_bytes);
   e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
   for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) {
     e = cudaStreamCreateWithFlags(&s->side[k], cudaStreamNonBlocking);
@@ -420,8 +384,9 @@ int ltjk_service_submit(ltjk_service *s, const ltjk_request *r, uint64_t *ticket
   auto j = std::make_unique<SvcJob>();
   j->req = *r;
   j->bytes = job_bytes(*r, r->ctx->nao, r->ctx->opts.precision == LTJK_MIXED);
-  if (j->bytes > s->arena.size)
-    return set_error(LTJK_EBUDGET, "request needs %zu bytes, budget is %zu", j->bytes, s->arena.size);
+  if (!s->arena.could_fit(j->bytes))
+    return set_error(LTJK_EBUDGET, "request needs %zu bytes (%zu rounded to the arena's %zu-byte blocks), "
+                     "usable budget is %zu", j->bytes, Arena::rounded(j->bytes), Arena::kAlign, s->arena.size);
   std::lock_guard<std::mutex> g(s->mu);
   if (s->stop) return set_error(LTJK_EINVAL, "service is shutting down");
   j->ticket = s->next_ticket++;

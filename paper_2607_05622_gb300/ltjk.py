@@ -45,7 +45,8 @@ class CtxStats(ctypes.Structure):
                 ("quartets_fp64", ctypes.c_int64), ("prim_quartets_kept", ctypes.c_int64),
                 ("cart_integrals_kept", ctypes.c_int64), ("eri_flops_per_build", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("eri_flops_fp64", ctypes.c_double),
-                ("cart_integrals_fp64", ctypes.c_int64)]
+                ("cart_integrals_fp64", ctypes.c_int64), ("grad_eri_flops", ctypes.c_double),
+                ("grad_eri_flops_fp64", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,6 +85,9 @@ SIGNATURES = {
     "ltjk_jk_build": ([_P, _I, _P, _P, _P, _P], _I),
     "ltjk_jk_build_noalloc": ([_P, _I, _P, _P, _P, _P], _I),
     "ltjk_jk_grad": ([_P, _I, _P, _P, _D, _D, _P, _P], _I),
+    "ltjk_jk_fock": ([_P, _I, _P, _D, _D, _P, _P], _I),
+    "ltjk_alu_peak": ([_I, _P, _P], _I),
+    "ltjk_jk_energy": ([_P, _I, _P, _P, _D, _D, _P, _P, _P], _I),
     "ltjk_shell_quartets": ([_P, _I, _P, _I, _P, _P], _I),
     "ltjk_class_program": ([_I, _I, _I, _I, _I, _P], _I),
     "ltjk_nsph": ([_P, _P], _I),
@@ -130,13 +134,17 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _dev(t: torch.Tensor, shape=None, name="tensor"):
+def _dev(t: torch.Tensor, shape=None, name="tensor", device=None):
+    """Device pointer of a contiguous CUDA float64 tensor of the given shape, on
+    GPU `device` when given (the library's kernels run on the context's GPU)."""
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
         raise ValueError(f"{name} must be a CUDA float64 tensor")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the context is on cuda:{device}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -145,6 +153,17 @@ def launch_count() -> int:
     c = ctypes.c_ulonglong(0)
     _check(lib().ltjk_launch_count(ctypes.byref(c)))
     return c.value
+
+
+ALU_FP32, ALU_FP64, ALU_DFLOAT_FMA, ALU_DFLOAT_DOT = 0, 1, 2, 3
+
+
+def alu_peak(kind: int, stream=None) -> float:
+    """ltjk_alu_peak: launch one arithmetic-throughput kernel on the stream;
+    returns its algorithmic flops (time it with CUDA events)."""
+    f = ctypes.c_double(0.0)
+    _check(lib().ltjk_alu_peak(int(kind), ctypes.byref(f), _stream(stream)))
+    return f.value
 
 
 def class_program(la: int, lb: int, lc: int, ld: int, deriv: int = 0) -> dict:
@@ -236,13 +255,13 @@ class Context:
 
     def jk_build(self, D: torch.Tensor, J=None, K=None, want_j=True, want_k=True, stream=None):
         nd, N = D.shape[0], self.nao
-        dp = _dev(D, (nd, N, N), "D")
+        dp = _dev(D, (nd, N, N), "D", device=self.device)
         if want_j and J is None:
             J = torch.empty_like(D)
         if want_k and K is None:
             K = torch.empty_like(D)
-        jp = _dev(J, (nd, N, N), "J") if want_j else None
-        kp = _dev(K, (nd, N, N), "K") if want_k else None
+        jp = _dev(J, (nd, N, N), "J", device=self.device) if want_j else None
+        kp = _dev(K, (nd, N, N), "K", device=self.device) if want_k else None
         _check(lib().ltjk_jk_build(self._h, nd, dp, jp, kp, _stream(stream)))
         return J, K
 
@@ -250,18 +269,40 @@ class Context:
         """ltjk_jk_build_noalloc: the same build with the library's fixed scratch array;
         the library allocates nothing (J and K are the caller's)."""
         nd, N = D.shape[0], self.nao
-        _check(lib().ltjk_jk_build_noalloc(self._h, nd, _dev(D, (nd, N, N), "D"),
-                                           _dev(J, (nd, N, N), "J"), _dev(K, (nd, N, N), "K"),
+        _check(lib().ltjk_jk_build_noalloc(self._h, nd, _dev(D, (nd, N, N), "D", device=self.device),
+                                           _dev(J, (nd, N, N), "J", device=self.device), _dev(K, (nd, N, N), "K", device=self.device),
                                            _stream(stream)))
         return J, K
 
+    def jk_fock(self, D: torch.Tensor, cJ=1.0, cK=0.0, F=None, stream=None):
+        """ltjk_jk_fock: F[q] = cJ J[D_q] + cK K[D_q]."""
+        nd, N = D.shape[0], self.nao
+        if F is None:
+            F = torch.empty_like(D)
+        _check(lib().ltjk_jk_fock(self._h, nd, _dev(D, (nd, N, N), "D", device=self.device), float(cJ),
+                                  float(cK), _dev(F, (nd, N, N), "F", device=self.device), _stream(stream)))
+        return F
+
+    def jk_energy(self, P: torch.Tensor, Q: torch.Tensor, cJ=1.0, cK=0.0, F=None, stream=None):
+        """ltjk_jk_energy: (E, F) with F = cJ J[Q] + cK K[Q] and E = sum_r <P_r, F_r>
+        (E a 0-dimensional device tensor)."""
+        nt, N = P.shape[0], self.nao
+        if F is None:
+            F = torch.empty_like(Q)
+        E = torch.empty((), dtype=torch.float64, device=P.device)
+        _check(lib().ltjk_jk_energy(self._h, nt, _dev(P, (nt, N, N), "P", device=self.device),
+                                    _dev(Q, (nt, N, N), "Q", device=self.device), float(cJ), float(cK),
+                                    _dev(F, (nt, N, N), "F", device=self.device),
+                                    _dev(E, (), "E", device=self.device), _stream(stream)))
+        return E, F
+
     def jk_grad(self, P: torch.Tensor, Q: torch.Tensor, cJ=1.0, cK=0.0, grad=None, stream=None):
         nt, N = P.shape[0], self.nao
-        pp = _dev(P, (nt, N, N), "P")
-        qp = _dev(Q, (nt, N, N), "Q")
+        pp = _dev(P, (nt, N, N), "P", device=self.device)
+        qp = _dev(Q, (nt, N, N), "Q", device=self.device)
         if grad is None:
             grad = torch.empty((self.natoms, 3), dtype=torch.float64, device=P.device)
-        gp = _dev(grad, (self.natoms, 3), "grad")
+        gp = _dev(grad, (self.natoms, 3), "grad", device=self.device)
         _check(lib().ltjk_jk_grad(self._h, nt, pp, qp, float(cJ), float(cK), gp, _stream(stream)))
         return grad
 
@@ -274,10 +315,10 @@ class Context:
         if D is None:
             D = torch.empty((nlap * npair, N, N), dtype=torch.float64, device=C_occ.device)
         _check(lib().ltjk_pseudo_densities(
-            self._h, no, nv, _dev(C_occ, (N, no), "C_occ"), _dev(C_vir, (N, nv), "C_vir"),
-            _dev(eps_occ, (no,), "eps_occ"), _dev(eps_vir, (nv,), "eps_vir"), npair,
-            _dev(X, (npair, no, nv), "X"), nlap, t.ctypes.data_as(_P),
-            _dev(D, (nlap * npair, N, N), "D"), _stream(stream)))
+            self._h, no, nv, _dev(C_occ, (N, no), "C_occ", device=self.device), _dev(C_vir, (N, nv), "C_vir", device=self.device),
+            _dev(eps_occ, (no,), "eps_occ", device=self.device), _dev(eps_vir, (nv,), "eps_vir", device=self.device), npair,
+            _dev(X, (npair, no, nv), "X", device=self.device), nlap, t.ctypes.data_as(_P),
+            _dev(D, (nlap * npair, N, N), "D", device=self.device), _stream(stream)))
         return D
 
     @property
@@ -290,7 +331,7 @@ class Context:
         """ltjk_sph_transform direction 0: T A[q] T^T (Cartesian matrices to spherical)."""
         nd, N, Ns = A.shape[0], self.nao, self.nsph
         B = torch.empty((nd, Ns, Ns), dtype=torch.float64, device=A.device)
-        _check(lib().ltjk_sph_transform(self._h, 0, nd, _dev(A, (nd, N, N), "A"), _dev(B, name="B"),
+        _check(lib().ltjk_sph_transform(self._h, 0, nd, _dev(A, (nd, N, N), "A", device=self.device), _dev(B, name="B", device=self.device),
                                         _stream(stream)))
         return B
 
@@ -298,7 +339,7 @@ class Context:
         """ltjk_sph_transform direction 1: T^T A[q] T (spherical densities to Cartesian)."""
         nd, N, Ns = A.shape[0], self.nao, self.nsph
         B = torch.empty((nd, N, N), dtype=torch.float64, device=A.device)
-        _check(lib().ltjk_sph_transform(self._h, 1, nd, _dev(A, (nd, Ns, Ns), "A"), _dev(B, name="B"),
+        _check(lib().ltjk_sph_transform(self._h, 1, nd, _dev(A, (nd, Ns, Ns), "A", device=self.device), _dev(B, name="B", device=self.device),
                                         _stream(stream)))
         return B
 
@@ -309,7 +350,7 @@ class Context:
         buf = torch.empty((int(max_vectors), N, N), dtype=torch.float64, device=f"cuda:{self.device}")
         naux = ctypes.c_int(0)
         res = ctypes.c_double(0.0)
-        _check(lib().ltjk_cd_factor(self._h, float(delta), int(max_vectors), _dev(buf, name="B"),
+        _check(lib().ltjk_cd_factor(self._h, float(delta), int(max_vectors), _dev(buf, name="B", device=self.device),
                                     ctypes.byref(naux), ctypes.byref(res), _stream(stream)))
         return buf[: naux.value], naux.value, res.value
 
@@ -323,10 +364,10 @@ class Context:
         U = torch.empty((nq, N, no), dtype=torch.float64, device=C_occ.device)
         V = torch.empty_like(U)
         _check(lib().ltjk_pseudo_density_factors(
-            self._h, no, nv, _dev(C_occ, (N, no), "C_occ"), _dev(C_vir, (N, nv), "C_vir"),
-            _dev(eps_occ, (no,), "eps_occ"), _dev(eps_vir, (nv,), "eps_vir"), npair,
-            _dev(X, (npair, no, nv), "X"), t.shape[0], t.ctypes.data_as(_P), _dev(U, name="U"),
-            _dev(V, name="V"), _stream(stream)))
+            self._h, no, nv, _dev(C_occ, (N, no), "C_occ", device=self.device), _dev(C_vir, (N, nv), "C_vir", device=self.device),
+            _dev(eps_occ, (no,), "eps_occ", device=self.device), _dev(eps_vir, (nv,), "eps_vir", device=self.device), npair,
+            _dev(X, (npair, no, nv), "X", device=self.device), t.shape[0], t.ctypes.data_as(_P), _dev(U, name="U", device=self.device),
+            _dev(V, name="V", device=self.device), _stream(stream)))
         return U, V
 
     def cd_jk(self, B: torch.Tensor, U: torch.Tensor, V: torch.Tensor, J=None, K=None, stream=None):
@@ -339,9 +380,9 @@ class Context:
             J = torch.empty((nd, N, N), dtype=torch.float64, device=V.device)
         if K is None:
             K = torch.empty((nd, N, N), dtype=torch.float64, device=V.device)
-        _check(lib().ltjk_cd_jk(self._h, naux, _dev(B, (naux, N, N), "B"), nd, rank, nu,
-                                _dev(U, (nu, N, rank), "U"), _dev(V, (nd, N, rank), "V"),
-                                _dev(J, (nd, N, N), "J"), _dev(K, (nd, N, N), "K"), _stream(stream)))
+        _check(lib().ltjk_cd_jk(self._h, naux, _dev(B, (naux, N, N), "B", device=self.device), nd, rank, nu,
+                                _dev(U, (nu, N, rank), "U", device=self.device), _dev(V, (nd, N, rank), "V", device=self.device),
+                                _dev(J, (nd, N, N), "J", device=self.device), _dev(K, (nd, N, N), "K", device=self.device), _stream(stream)))
         return J, K
 
     def laplace_fock(self, J, K, C_left, C_right, cJ=2.0, cK=-1.0, F=None, stream=None):
@@ -350,9 +391,9 @@ class Context:
         nl, nr = C_left.shape[1], C_right.shape[1]
         if F is None:
             F = torch.empty((nd, nl, nr), dtype=torch.float64, device=J.device)
-        _check(lib().ltjk_laplace_fock(self._h, nd, _dev(J, (nd, N, N), "J"), _dev(K, (nd, N, N), "K"),
-                                       float(cJ), float(cK), nl, _dev(C_left, (N, nl), "C_left"), nr,
-                                       _dev(C_right, (N, nr), "C_right"), _dev(F, (nd, nl, nr), "F"),
+        _check(lib().ltjk_laplace_fock(self._h, nd, _dev(J, (nd, N, N), "J", device=self.device), _dev(K, (nd, N, N), "K", device=self.device),
+                                       float(cJ), float(cK), nl, _dev(C_left, (N, nl), "C_left", device=self.device), nr,
+                                       _dev(C_right, (N, nr), "C_right", device=self.device), _dev(F, (nd, nl, nr), "F", device=self.device),
                                        _stream(stream)))
         return F
 
@@ -365,7 +406,7 @@ class Context:
             sizes.append(int(np.prod([(int(ls[s]) + 1) * (int(ls[s]) + 2) // 2 for s in (a, b, c, d)])))
         out = torch.zeros(max(sum(sizes), 1), dtype=torch.float64, device=f"cuda:{self.device}")
         _check(lib().ltjk_shell_quartets(self._h, q.shape[0], q.ctypes.data_as(_P), int(precision),
-                                         _dev(out, None, "out"), _stream(stream)))
+                                         _dev(out, None, "out", device=self.device), _stream(stream)))
         torch.cuda.current_stream().synchronize()
         res, off = [], 0
         host = out.cpu().numpy()
@@ -379,19 +420,19 @@ class Context:
 class JKEnergy(torch.autograd.Function):
     """E = sum_r <P_r, cJ J[Q_r] + cK K[Q_r]> = sum_r [cJ J(P_r,Q_r) + cK K(P_r,Q_r)].
 
-    forward(coords, P, Q, mol, cJ, cK, opts) builds a context at ``coords``;
-    backward gives dE/dcoords from ltjk_jk_grad (Eq. jkderiv) and
-    dE/dP_r = cJ J[Q_r] + cK K[Q_r], dE/dQ_r = cJ J[P_r] + cK K[P_r] from
-    ltjk_jk_build (the adjoint of a J/K build is a J/K build)."""
+    forward(coords, P, Q, mol, cJ, cK, opts) builds a context at ``coords`` and
+    evaluates E with ltjk_jk_energy; backward gives dE/dcoords from
+    ltjk_jk_grad (Eq. jkderiv) and dE/dP_r = cJ J[Q_r] + cK K[Q_r] (kept from
+    the forward pass), dE/dQ_r = cJ J[P_r] + cK K[P_r] from ltjk_jk_fock (the
+    adjoint of a J/K build is a J/K build).  The binding only scales the
+    library's results by the upstream gradient."""
 
     @staticmethod
     def forward(ctx_, coords, P, Q, mol, cJ=1.0, cK=0.0, opts=None):
         opts = dict(opts or {})
         m = mol.with_coords(coords.detach().cpu().numpy().astype(np.float64))
         c = Context(m, **opts)
-        J, K = c.jk_build(Q.detach().contiguous())
-        F = cJ * J + cK * K
-        E = torch.sum(P.detach() * F)
+        E, F = c.jk_energy(P.detach().contiguous(), Q.detach().contiguous(), cJ, cK)
         ctx_.save_for_backward(P, Q, F)
         ctx_.c = c
         ctx_.cJ, ctx_.cK = cJ, cK
@@ -409,8 +450,7 @@ class JKEnergy(torch.autograd.Function):
         if ctx_.needs_input_grad[1]:
             gP = F * gE
         if ctx_.needs_input_grad[2]:
-            J, K = c.jk_build(P.detach().contiguous())
-            gQ = (ctx_.cJ * J + ctx_.cK * K) * gE
+            gQ = c.jk_fock(P.detach().contiguous(), ctx_.cJ, ctx_.cK) * gE
         return gc, gP, gQ, None, None, None, None
 
 
@@ -476,8 +516,8 @@ class Service:
             J = torch.empty_like(D)
         if K is None:
             K = torch.empty_like(D)
-        req = _Request(REQ_JK, ctx._h.value, nd, _dev(D, (nd, N, N), "D").value,
-                       _dev(J, (nd, N, N), "J").value, _dev(K, (nd, N, N), "K").value,
+        req = _Request(REQ_JK, ctx._h.value, nd, _dev(D, (nd, N, N), "D", device=ctx.device).value,
+                       _dev(J, (nd, N, N), "J", device=ctx.device).value, _dev(K, (nd, N, N), "K", device=ctx.device).value,
                        None, None, 0.0, 0.0, None)
         return self._submit(req, (ctx, D, J, K)), J, K
 
@@ -486,8 +526,8 @@ class Service:
         if grad is None:
             grad = torch.empty((ctx.natoms, 3), dtype=torch.float64, device=P.device)
         req = _Request(REQ_GRAD, ctx._h.value, nt, None, None, None,
-                       _dev(P, (nt, N, N), "P").value, _dev(Q, (nt, N, N), "Q").value,
-                       float(cJ), float(cK), _dev(grad, (ctx.natoms, 3), "grad").value)
+                       _dev(P, (nt, N, N), "P", device=ctx.device).value, _dev(Q, (nt, N, N), "Q", device=ctx.device).value,
+                       float(cJ), float(cK), _dev(grad, (ctx.natoms, 3), "grad", device=ctx.device).value)
         return self._submit(req, (ctx, P, Q, grad)), grad
 
     def poll(self, ticket):

@@ -14,7 +14,8 @@ IEEE FP64 on the same GPU:
   3. the stream replayed in real time into the service by a pool of frontend
      threads that build each request's context and densities on arrival;
      latency = completion time - arrival time (context creation and density
-     formation included).
+     formation included); with --saturated every request arrives at once, so
+     the throughput is the service's capacity.
 
 Prints one JSON line.
 """
@@ -61,18 +62,12 @@ def sample_index(n, k, seed):
     return rng.integers(0, n, size=min(k, n))
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--requests", type=int, default=256)
-    ap.add_argument("--nao-max", type=int, default=730)
-    ap.add_argument("--budget-gb", type=float, default=150.0)
-    ap.add_argument("--load", type=float, default=0.8)
-    ap.add_argument("--frontend-threads", type=int, default=4)
-    args = ap.parse_args()
-    import torch
-    from paper_2607_05622_gb300 import ltjk as L
-    dev = torch.device("cuda:0")
-    reqs = W.serving_requests(args.requests, seed=5, nao_hi=args.nao_max, rate_hz=1.0)
+def run_stream(L, torch, dev, nreq=256, nao_hi=730, budget_gb=150.0, load=0.8, frontend_threads=4,
+               seed=5, saturated=False):
+    """The three passes above on one request list; returns the result dict.
+    saturated: every request arrives at time 0 (offered load above capacity),
+    so the throughput measured is the service's capacity, not the arrival rate."""
+    reqs = W.serving_requests(nreq, seed=seed, nao_hi=nao_hi, rate_hz=1.0)
     ref = []
     seq_fp64 = []
     # 1. sequential plain FP64
@@ -108,16 +103,16 @@ def main():
         ctx.close()
         del inp
     capacity = len(reqs) / sum(seq_mixed)
-    rate = args.load * capacity
+    rate = load * capacity
     # arrival times rescaled to the chosen rate (same Poisson draws)
     base = np.array([r["arrival"] for r in reqs])
-    arrivals = base * (1.0 / rate) / (base[-1] / len(reqs))
+    arrivals = np.zeros(len(reqs)) if saturated else base * (1.0 / rate) / (base[-1] / len(reqs))
     # 3. served stream: a pool of host threads (a serving frontend) builds each
     # request's context and densities when it arrives and submits it; the main
     # thread collects completions.  Latency = completion - arrival.
     import concurrent.futures as cf
     import threading
-    svc = L.Service(int(args.budget_gb * (1 << 30)))
+    svc = L.Service(int(budget_gb * (1 << 30)))
     pending = {}
     lock = threading.Lock()
     lat, errs_j, errs_k, errs_g = [], [], [], []
@@ -162,7 +157,7 @@ def main():
             with lock:
                 del pending[tk]
 
-    with cf.ThreadPoolExecutor(max_workers=args.frontend_threads) as pool:
+    with cf.ThreadPoolExecutor(max_workers=frontend_threads) as pool:
         futs = [pool.submit(arrive, i) for i in range(len(reqs))]
         while len(lat) < len(reqs):
             harvest()
@@ -176,12 +171,13 @@ def main():
     lat_ms = sorted(1e3 * x for x in lat)
     pct = lambda p: lat_ms[min(len(lat_ms) - 1, int(round(p * (len(lat_ms) - 1))))]  # noqa: E731
     nao = [r["mol"].nao for r in reqs]
-    out = {
+    return {
         "metric": "serving: p50/p99 latency and throughput, mixed precision, continuous batching",
         "requests": len(reqs), "jk": sum(r["kind"] == "jk" for r in reqs),
         "grad": sum(r["kind"] == "grad" for r in reqs),
         "nao_min": min(nao), "nao_median": int(np.median(nao)), "nao_max": max(nao),
-        "arrival_rate_hz": rate, "offered_load": args.load,
+        "arrivals": "all at t = 0 (saturated)" if saturated else f"Poisson at {load} x capacity",
+        "arrival_rate_hz": None if saturated else rate, "offered_load": None if saturated else load,
         "p50_ms": pct(0.5), "p99_ms": pct(0.99), "mean_ms": statistics.mean(lat_ms),
         "throughput_rps": len(reqs) / span, "span_s": span,
         "sequential_fp64": {"throughput_rps": len(reqs) / sum(seq_fp64),
@@ -193,8 +189,23 @@ def main():
                           "grad_max_rel_to_max": max(errs_g) if errs_g else None,
                           "how": "4096 sampled elements per J/K result, full gradient"},
         "service": {k2: st[k2] for k2 in ("steps", "launches", "bytes_peak", "budget", "completed")},
-        "budget_gb": args.budget_gb, "frontend_threads": args.frontend_threads,
+        "budget_gb": budget_gb, "frontend_threads": frontend_threads,
     }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--nao-max", type=int, default=730)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--saturated", action="store_true", help="every request arrives at time 0")
+    ap.add_argument("--frontend-threads", type=int, default=4)
+    args = ap.parse_args()
+    import torch
+    from paper_2607_05622_gb300 import ltjk as L
+    out = run_stream(L, torch, torch.device("cuda:0"), args.requests, args.nao_max, args.budget_gb, args.load,
+                     args.frontend_threads, saturated=args.saturated)
     print(json.dumps(out))
 
 

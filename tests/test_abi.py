@@ -149,7 +149,7 @@ def test_null_handles_are_rejected_before_any_device_work(L):
     lib = L.lib()
     skip = {"ltjk_last_error", "ltjk_version", "ltjk_context_create", "ltjk_service_create",
             "ltjk_laplace_quadrature", "ltjk_laplace_minimax", "ltjk_laplace_shift",
-            "ltjk_class_program", "ltjk_launch_count"}
+            "ltjk_class_program", "ltjk_launch_count", "ltjk_alu_peak"}
     checked = 0
     for name, (args, _) in L.SIGNATURES.items():
         if name in skip:
@@ -164,6 +164,9 @@ def test_null_handles_are_rejected_before_any_device_work(L):
     assert lib.ltjk_launch_count(None) == L.EINVAL
     assert lib.ltjk_class_program(0, 0, 0, 0, 0, None) == L.EINVAL
     assert lib.ltjk_laplace_shift(0, None, None, 0.0, None) == L.EINVAL
+    f = ctypes.c_double(0.0)
+    assert lib.ltjk_alu_peak(4, ctypes.byref(f), None) == L.EINVAL
+    assert lib.ltjk_alu_peak(0, None, None) == L.EINVAL
 
 
 def test_last_error_is_per_thread(L):

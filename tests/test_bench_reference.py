@@ -28,6 +28,14 @@ def _check_line(d, gpus):
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"].startswith("chain 200 AO")
+    # the same metric string and workload description as the GPU arm, so the
+    # two lines can be divided
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2607_05622_gb300 import workloads as W
+    assert d["metric"] == bench.METRIC
+    cfg = bench.bench_config(W.config2(), "mixed")
+    assert {k: d["config"][k] for k in cfg} == cfg
 
 
 def test_reference_arm_one_rank():

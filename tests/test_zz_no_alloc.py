@@ -45,6 +45,34 @@ def test_noalloc_matches_jk_build_twice(L, precision):
         assert rel(J, J0) <= TOL64 and rel(K, K0) <= TOL64, (call, rel(J, J0), rel(K, K0))
 
 
+def test_noalloc_allocates_nothing(L):
+    """In a fresh context, before any other build: the context's device memory
+    does not grow, and after one warm-up call (which loads the kernels) a
+    second call leaves the device's free memory unchanged."""
+    wl = W.small_chain(2, 2, seed=4, tau=1e-12)
+    ctx = L.Context(wl.mol, schwarz_tau=1e-12, mixed_tau=1e-6, precision=L.MIXED)
+    N = wl.mol.nao
+    D = torch.from_numpy(np.random.default_rng(13).standard_normal((8, N, N))).to("cuda:0")
+    J, K = torch.empty_like(D), torch.empty_like(D)
+    bytes0 = ctx.stats()["device_bytes"]
+    ctx.jk_build_noalloc(D, J, K)
+    torch.cuda.synchronize()
+    assert ctx.stats()["device_bytes"] == bytes0
+    free0 = torch.cuda.mem_get_info()[0]
+    J2, K2 = torch.full_like(D, np.nan), torch.full_like(D, np.nan)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    ctx.jk_build_noalloc(D, J2, K2)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free1
+    assert ctx.stats()["device_bytes"] == bytes0
+    assert free0 >= free1
+    J0, K0 = ctx.jk_build(D)  # the allocating build, afterwards
+    torch.cuda.synchronize()
+    assert rel(J2, J0) <= TOL64 and rel(K2, K0) <= TOL64
+    assert rel(J, J0) <= TOL64 and rel(K, K0) <= TOL64
+
+
 def test_noalloc_rejects_oversize(L):
     w = W.config2()
     ctx = L.Context(w.mol, schwarz_tau=1e-12)
