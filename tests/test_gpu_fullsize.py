@@ -3,6 +3,8 @@
 (128 densities, mixed precision) against oracle blocks computed one by one
 from the definition; the 200-AO gradient against central finite differences
 of the GPU FP64 energy and translational invariance."""
+import os
+
 import numpy as np
 import pytest
 
@@ -105,3 +107,22 @@ def test_chain200_gradient_fd(L):
         fd = (gpu_energy(L, mol.with_coords(cp), P, Q, wl.cJ, wl.cK, tau)
               - gpu_energy(L, mol.with_coords(cm), P, Q, wl.cJ, wl.cK, tau)) / (2 * h)
         assert abs(g[atom, x] - fd) <= 1e-7 * gmax + 1e-9, (atom, x, g[atom, x], fd)
+
+
+def test_chain200_gradient_row_vs_oracle(L):
+    """The full-size gradient (200-AO chain, 16 terms, unscreened) against the
+    oracle's explicit four-centre derivative integrals for one atom's row,
+    stored by tests/golden/make_grad_chain200.py (the oracle needs minutes for
+    it): FP64 gate relative to the largest gradient component."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "grad_chain200_atom19.txt")
+    rows = [l for l in open(path) if not l.startswith("#")]
+    ref = np.array([float(v) for v in rows[0].split()])
+    wl = W.config4()
+    P, Q = dev(wl.P), dev(wl.Q)
+    for prec in (L.FP64, L.FP64_NATIVE):
+        c = L.Context(wl.mol, schwarz_tau=0.0, precision=prec)
+        g = c.jk_grad(P, Q, wl.cJ, wl.cK).cpu().numpy()
+        gmax = np.abs(g).max()
+        err = np.abs(g[19] - ref).max() / gmax
+        print(f"precision {prec}: atom 19 row vs oracle {err:.2e} of max|g| = {gmax:.3g}")
+        assert err <= 1e-10, (prec, g[19], ref)
