@@ -207,11 +207,20 @@ ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
   int S = 1;
   while (S < 32 && S < width) S *= 2;
   cl.G = 32 / S;
+  cl.T = 32;
   for (;;) {
-    size_t bytes = warp_smem_bytes(p, cl.G, real_bytes);
+    size_t bytes = warp_smem_bytes(p, cl.G, cl.T, real_bytes);
     cl.smem_per_warp = (int)bytes;
     if (bytes <= (size_t)kSmemBudget || cl.G == 1) break;
     cl.G /= 2;
+  }
+  // a smaller primitive table for classes whose warps would otherwise be
+  // limited by shared memory (16 warps of 128 registers fit an SM): the
+  // set-up runs on fewer lanes at a time, a few per cent of a heavy quartet
+  while (cl.T > 8 && cl.smem_per_warp > kSmemPerSM / 16 &&
+         (size_t)(cl.T / 2) * pt_stride(p) * real_bytes >= (size_t)kDigestTableBytes) {
+    cl.T /= 2;
+    cl.smem_per_warp = (int)warp_smem_bytes(p, cl.G, cl.T, real_bytes);
   }
   cl.warps = std::max(1, std::min(4, kSmemBudget / std::max(cl.smem_per_warp, 1)));
   return cl;

@@ -224,23 +224,25 @@ struct ClassLaunch {
   int G;        // primitive-quartet groups per warp (S = 32 / G lanes each)
   int warps;    // warps per CTA
   int smem_per_warp;  // bytes
+  int T;        // primitive-table entries (set-up of T primitive quartets at a time)
 };
 
-// Shared memory one warp needs for class program p with G groups, in bytes:
-// primitive table, G accumulator sets and the work region (Real), then for
-// the gradient the Gamma block of one quartet (double).
-__host__ __device__ inline size_t warp_smem_bytes(const ClassProg &p, int G, size_t real_bytes) {
+// Shared memory one warp needs for class program p with G groups and a T-entry
+// primitive table, in bytes: primitive table, G accumulator sets and the work
+// region (Real), then for the gradient the Gamma block of one quartet (double).
+__host__ __device__ inline size_t gamma_offset(const ClassProg &p, int G, int T, size_t real_bytes) {
   int work = G * p.vrr_size > p.hrr_size ? G * p.vrr_size : p.hrr_size;
-  size_t b = (size_t)(32 * pt_stride(p) + G * p.acc_total + work) * real_bytes;
-  b = (b + 15) / 16 * 16;
+  size_t b = (size_t)(T * pt_stride(p) + G * p.acc_total + work) * real_bytes;
+  return (b + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t warp_smem_bytes(const ClassProg &p, int G, int T, size_t real_bytes) {
+  size_t b = gamma_offset(p, G, T, real_bytes);
   if (p.deriv) b += (size_t)p.nout * sizeof(double);
   return (b + 15) / 16 * 16;
 }
-__host__ __device__ inline size_t gamma_offset(const ClassProg &p, int G, size_t real_bytes) {
-  int work = G * p.vrr_size > p.hrr_size ? G * p.vrr_size : p.hrr_size;
-  size_t b = (size_t)(32 * pt_stride(p) + G * p.acc_total + work) * real_bytes;
-  return (b + 15) / 16 * 16;
-}
+// The digestion tabulates its output offsets in the dead primitive table:
+// at most 10 placements x 9 groups x 4 outputs of int2.
+constexpr int kDigestTableBytes = 10 * 9 * 4 * 8;
 
 // ------------------------------------------- stage 1: one primitive quartet
 // Base values [00|00]^(m) = 2 pi^{5/2} K_AB K_CD c.. / (zeta eta sqrt(zeta+eta))
@@ -355,12 +357,12 @@ __device__ __forceinline__ void stage1(const DevBasis &B, const ClassProg &p, Re
 // the warp's shared memory and returns a pointer to the output block (nout
 // Reals, row-major [na][nb][nc][nd], or 9 such blocks for derivatives).
 template <typename Real>
-__device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const ClassProg &p, int G,
+__device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const ClassProg &p, int G, int T,
                                Real *sm, int ip, int jp, int lane) {
   const int S = 32 / G, g = lane / S, s = lane % S;
   const int stride = pt_stride(p), nh = p.nh;
-  Real *ptab = sm;                              // [32][stride]
-  Real *accs = ptab + 32 * stride;              // [G][acc_total]; group 0's last
+  Real *ptab = sm;                              // [T][stride]
+  Real *accs = ptab + T * stride;               // [G][acc_total]; group 0's last
   Real *acc0 = accs + (G - 1) * p.acc_total;
   Real *work = acc0 + p.acc_total;              // VRR regions / HRR slots
   Real *my_acc = accs + (G - 1 - g) * p.acc_total;
@@ -373,16 +375,16 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
 
   for (int t = lane; t < G * p.acc_total; t += 32) accs[t] = zero_real<Real>();
 
-  for (int c0 = 0; c0 < npq; c0 += 32) {
+  for (int c0 = 0; c0 < npq; c0 += T) {
     // stage 1: base values and coefficients, one primitive quartet per lane
     const int pq = c0 + lane;
-    if (pq < npq) {
+    if (lane < T && pq < npq) {
       const int ia = pp0 + pq / nqq, ic = qq0 + pq % nqq;
       stage1<Real>(B, p, ptab + lane * stride, ia, ic, sab, scd);
     }
     __syncwarp();
     // stage 2: recurrences, G primitive quartets at a time
-    const int nchunk = min(32, npq - c0);
+    const int nchunk = min(T, npq - c0);
     for (int r0 = 0; r0 < nchunk; r0 += G) {
       const int loc = r0 + g;
       const bool active = loc < nchunk;
@@ -557,7 +559,7 @@ __device__ __forceinline__ void digest_place(const Real *__restrict__ I, const R
 // The ten placements of one quartet.  tab is scratch shared memory of the warp
 // (its primitive table, dead between the recurrences of two kets) for the
 // per-output offsets of every placement: at most 10 x 9 groups x 4 outputs of
-// 8 bytes, 2880 bytes, below the smallest primitive table (32 x 24 FP32 words).
+// 8 bytes, kDigestTableBytes; the launch keeps the table at least that large.
 // The output offsets x*N*nd + y*nd fit 32 bits for every size the build accepts.
 template <typename Real>
 __device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], const int n[4], int N,
@@ -639,7 +641,7 @@ __global__ void __launch_bounds__(128, 4) quartet_kernel(DevProgs PR, ClassLaunc
   const ClassProg &p = CL.p;
   unsigned char *wbase = smem_raw + (size_t)warp * CL.smem_per_warp;
   Real *sm = reinterpret_cast<Real *>(wbase);
-  double *gam = reinterpret_cast<double *>(wbase + gamma_offset(p, CL.G, sizeof(Real)));
+  double *gam = reinterpret_cast<double *>(wbase + gamma_offset(p, CL.G, CL.T, sizeof(Real)));
   for (int it = blockIdx.x * CL.warps + warp; it < T.total; it += gridDim.x * CL.warps) {
     int jb = 0;  // job holding item it (jobs are few; linear search in the parameter block)
     while (jb + 1 < T.njobs && it >= T.j[jb + 1].first) ++jb;
@@ -653,7 +655,7 @@ __global__ void __launch_bounds__(128, 4) quartet_kernel(DevProgs PR, ClassLaunc
     for (int kk = 0; kk < W.nk; ++kk) {
       const int jp = W.k0 + kk;
       const int2 scd = B.pair_sh[jp];
-      Real *acc0 = quartet_block<Real>(B, PR, p, CL.G, sm, W.bra, jp, lane);
+      Real *acc0 = quartet_block<Real>(B, PR, p, CL.G, CL.T, sm, W.bra, jp, lane);
       const int sh[4] = {sab.x, sab.y, scd.x, scd.y};
       int off[4], n[4];
       for (int t = 0; t < 4; ++t) {
