@@ -197,33 +197,52 @@ int device_programs(int dev, DevProgs *out, const double **boys, const float2 **
 // Launch configuration of one class program: groups per warp from the average
 // width of a recurrence level, warps per CTA from the shared-memory budget.
 ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
-  ClassLaunch cl{};
-  cl.p = p;
-  int ninstr = 0;
+  // Candidate layouts: G groups of S lanes (one primitive quartet per group,
+  // its S lanes over the independent steps of each recurrence level) and a
+  // T-entry primitive table (G <= T; T shrinks from 32 while the warp's shared
+  // memory would keep fewer than 16 warps on an SM, as long as the digestion's
+  // offset table still fits in it).  Cost per primitive quartet, in warp
+  // iterations: sum over levels of ceil(width / 2S) x S / 32 (each lane takes
+  // two steps per iteration, G = 32/S quartets share the warp), scaled by
+  // 12 / (warps per SM) when shared memory allows fewer than 12 warps.  The
+  // cheapest layout wins; narrow levels favour small S, large programs
+  // large S (their slots are G-fold).
   const ProgramSet &ps = g_prog.ps;
-  if (p.nvrr_level > 0)
-    ninstr = ps.levels[p.vrr_level0 + p.nvrr_level] - ps.levels[p.vrr_level0];
-  double width = p.nvrr_level > 0 ? double(ninstr) / p.nvrr_level : 0.0;
-  int S = 1;
-  while (S < 32 && S < width) S *= 2;
-  cl.G = 32 / S;
-  cl.T = 32;
-  for (;;) {
-    size_t bytes = warp_smem_bytes(p, cl.G, cl.T, real_bytes);
-    cl.smem_per_warp = (int)bytes;
-    if (bytes <= (size_t)kSmemBudget || cl.G == 1) break;
-    cl.G /= 2;
-  }
-  // a smaller primitive table for classes whose warps would otherwise be
-  // limited by shared memory (16 warps of 128 registers fit an SM): the
-  // set-up runs on fewer lanes at a time, a few per cent of a heavy quartet
-  while (cl.T > 8 && cl.smem_per_warp > kSmemPerSM / 16 &&
-         (size_t)(cl.T / 2) * pt_stride(p) * real_bytes >= (size_t)kDigestTableBytes) {
-    cl.T /= 2;
+  ClassLaunch best{};
+  double best_cost = 1e300;
+  for (int S = 32; S >= 1; S /= 2) {
+    ClassLaunch cl{};
+    cl.p = p;
+    cl.G = 32 / S;
+    cl.T = 32;
     cl.smem_per_warp = (int)warp_smem_bytes(p, cl.G, cl.T, real_bytes);
+    while (cl.T > 8 && cl.T / 2 >= cl.G && cl.smem_per_warp > kSmemPerSM / 16 &&
+           (size_t)(cl.T / 2) * pt_stride(p) * real_bytes >= (size_t)kDigestTableBytes) {
+      cl.T /= 2;
+      cl.smem_per_warp = (int)warp_smem_bytes(p, cl.G, cl.T, real_bytes);
+    }
+    if (cl.smem_per_warp > kSmemBudget) continue;
+    double cost = 0.0;
+    for (int L = 0; L < p.nvrr_level; ++L) {
+      const int w = ps.levels[p.vrr_level0 + L + 1] - ps.levels[p.vrr_level0 + L];
+      cost += (double)((w + 2 * S - 1) / (2 * S)) * S / 32.0;
+    }
+    cost += 1.0 / 32.0;  // per-quartet overheads: set-up share, syncs
+    const int warps_sm = std::min(16, kSmemPerSM / (cl.smem_per_warp + kSmemPerCTAReserved));
+    if (warps_sm < 12) cost *= 12.0 / std::max(warps_sm, 1);
+    if (cost < best_cost * 0.98) {  // a smaller S must win by 2 %: larger S needs less shared memory
+      best_cost = cost;
+      best = cl;
+    }
   }
-  cl.warps = std::max(1, std::min(4, kSmemBudget / std::max(cl.smem_per_warp, 1)));
-  return cl;
+  if (best_cost == 1e300) {  // nothing within the budget: one group, smallest table
+    best.p = p;
+    best.G = 1;
+    best.T = 8;
+    best.smem_per_warp = (int)warp_smem_bytes(p, 1, 8, real_bytes);
+  }
+  best.warps = std::max(1, std::min(4, kSmemBudget / std::max(best.smem_per_warp, 1)));
+  return best;
 }
 
 // Warps per CTA that put the most warps on an SM, given the shared memory one
