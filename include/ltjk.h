@@ -269,7 +269,8 @@ int ltjk_jk_fock(ltjk_ctx *ctx, int ndens, const double *D, double cJ, double cK
    cK K[Q] from ltjk_jk_fock.  P, Q [nterms][N][N] device; F [nterms][N][N]
    device (written, nullable: then kept in scratch); E one device double
    (overwritten).  The sum over elements is taken in a fixed order (no
-   atomics), so E is reproducible for a given F.  1 <= nterms <= 4096. */
+   atomics); F itself carries the build's atomic accumulation order, so two
+   calls agree to rounding.  1 <= nterms <= 4096. */
 int ltjk_jk_energy(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, double cJ,
                    double cK, double *F, double *E, ltjk_stream stream);
 

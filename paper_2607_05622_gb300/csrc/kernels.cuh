@@ -605,26 +605,43 @@ __device__ void gamma_block(const JKArgs &a, double *gam, const int off[4], cons
                             double w, int N, int lane) {
   const int nq = n[0] * n[1] * n[2] * n[3];
   const int nt = a.nd;
-  for (int e = lane; e < nq; e += 32) {
-    const int l = e % n[3], k = (e / n[3]) % n[2], j = (e / (n[3] * n[2])) % n[1],
-              i = e / (n[3] * n[2] * n[1]);
-    const size_t mu = off[0] + i, nu = off[1] + j, ka = off[2] + k, rho = off[3] + l;
+  // L lanes per element, each over terms r = sub, sub + L, ... (consecutive
+  // lanes read consecutive terms: the term index is innermost in P and Q),
+  // then a butterfly sum inside the L-lane group; 32 / L elements per pass.
+  // Light classes have only a few elements per quartet, so lanes over
+  // elements alone left most of the warp idle through all the terms.
+  const int L = nt >= 32 ? 32 : nt > 16 ? 32 : nt > 8 ? 16 : nt > 4 ? 8 : nt > 2 ? 4 : nt > 1 ? 2 : 1;
+  const int E = 32 / L, sub = lane % L, eg = lane / L;
+  for (int e0 = 0; e0 < nq; e0 += E) {
+    const int e = e0 + eg;
     double g = 0.0;
-    for (int r = 0; r < nt; ++r) {
-      const double *P = a.P + r, *Q = a.Q + r;
+    if (e < nq) {
+      const int l = e % n[3], k = (e / n[3]) % n[2], j = (e / (n[3] * n[2])) % n[1],
+                i = e / (n[3] * n[2] * n[1]);
+      const size_t mu = off[0] + i, nu = off[1] + j, ka = off[2] + k, rho = off[3] + l;
+      for (int r = sub; r < nt; r += L) {
+        const double *P = a.P + r, *Q = a.Q + r;
 #define PX(x, y) __ldg(P + ((x) * N + (y)) * nt)
 #define QX(x, y) __ldg(Q + ((x) * N + (y)) * nt)
-      const double gJ = (PX(mu, nu) + PX(nu, mu)) * (QX(ka, rho) + QX(rho, ka)) +
-                        (PX(ka, rho) + PX(rho, ka)) * (QX(mu, nu) + QX(nu, mu));
-      const double gK = PX(mu, ka) * QX(nu, rho) + PX(nu, ka) * QX(mu, rho) +
-                        PX(mu, rho) * QX(nu, ka) + PX(nu, rho) * QX(mu, ka) +
-                        PX(ka, mu) * QX(rho, nu) + PX(rho, mu) * QX(ka, nu) +
-                        PX(ka, nu) * QX(rho, mu) + PX(rho, nu) * QX(ka, mu);
+        // a zero coefficient skips its images (warp-uniform branches)
+        if (a.cJ != 0.0) {
+          const double gJ = (PX(mu, nu) + PX(nu, mu)) * (QX(ka, rho) + QX(rho, ka)) +
+                            (PX(ka, rho) + PX(rho, ka)) * (QX(mu, nu) + QX(nu, mu));
+          g = fma(a.cJ, gJ, g);
+        }
+        if (a.cK != 0.0) {
+          const double gK = PX(mu, ka) * QX(nu, rho) + PX(nu, ka) * QX(mu, rho) +
+                            PX(mu, rho) * QX(nu, ka) + PX(nu, rho) * QX(mu, ka) +
+                            PX(ka, mu) * QX(rho, nu) + PX(rho, mu) * QX(ka, nu) +
+                            PX(ka, nu) * QX(rho, mu) + PX(rho, nu) * QX(ka, mu);
+          g = fma(a.cK, gK, g);
+        }
 #undef PX
 #undef QX
-      g = fma(a.cJ, gJ, fma(a.cK, gK, g));
+      }
     }
-    gam[e] = w * g;
+    for (int o = L >> 1; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    if (sub == 0 && e < nq) gam[e] = w * g;
   }
 }
 

@@ -93,6 +93,6 @@ def test_jk_energy(L, oracle, chain):
     scale = float(np.sum(np.abs(Pm * Fr)))
     assert abs(E.item() - Er) <= TOL64 * scale
     assert relerr(F.cpu().numpy(), Fr) <= TOL64
-    # the same energy twice: the reduction order is fixed
+    # a second call (into the caller's F) agrees to the rounding of the build
     E2, _ = ctx.jk_energy(dev(Pm), dev(D), cJ, cK, F=F)
-    assert E2.item() == E.item()
+    assert abs(E2.item() - E.item()) <= 1e-12 * scale
