@@ -566,18 +566,24 @@ def run_gpu(args, world, rank, local):
             "measured_peaks_tflops": peaks,
             "nominal_peaks_tflops": alu_peaks(2070.0, torch.cuda.get_device_properties(local).multi_processor_count)}
     extras = {}
-    if not args.no_extras and rank == 0:
-        extras["next_rows"] = measure_next_rows(ltjk, torch, stream, ctx, w, J, K, Co, Cv, xmin, xmax, peaks)
-        tq, _, _ = ltjk.laplace_quadrature(xmin, xmax, w.nlap)
-        extras["next_rows"]["cholesky_jk"] = measure_cd(ltjk, torch, stream, ctx, w, D, J, K, Co, Cv, eo, ev, X, tq,
-                                                        peaks)
-        extras["gradient"] = measure_gradient(ltjk, torch, dev, local, stream, prec, peaks)
-        extras["macrocycle_445"] = measure_macrocycle(ltjk, torch, dev, local, stream)
-        extras["water_fp64_single_request"] = measure_config1(ltjk, torch, dev, local, stream)
-        extras["serving"] = measure_serving(ltjk, torch, dev)
-        pc = extras["serving"]["paced"]
-        extras["latency"] = {"p50_ms": pc["p50_ms"], "p99_ms": pc["p99_ms"],
-                             "what": "serving stream, 0.8 x capacity, mixed precision (see serving.paced)"}
+    legs = set() if args.no_extras else set(args.legs.split(","))
+    if rank == 0:
+        if "next_rows" in legs:
+            extras["next_rows"] = measure_next_rows(ltjk, torch, stream, ctx, w, J, K, Co, Cv, xmin, xmax, peaks)
+            tq, _, _ = ltjk.laplace_quadrature(xmin, xmax, w.nlap)
+            extras["next_rows"]["cholesky_jk"] = measure_cd(ltjk, torch, stream, ctx, w, D, J, K, Co, Cv, eo, ev,
+                                                            X, tq, peaks)
+        if "gradient" in legs:
+            extras["gradient"] = measure_gradient(ltjk, torch, dev, local, stream, prec, peaks)
+        if "macrocycle" in legs:
+            extras["macrocycle_445"] = measure_macrocycle(ltjk, torch, dev, local, stream)
+        if "water" in legs:
+            extras["water_fp64_single_request"] = measure_config1(ltjk, torch, dev, local, stream)
+        if "serving" in legs:
+            extras["serving"] = measure_serving(ltjk, torch, dev)
+            pc = extras["serving"]["paced"]
+            extras["latency"] = {"p50_ms": pc["p50_ms"], "p99_ms": pc["p99_ms"],
+                                 "what": "serving stream, 0.8 x capacity, mixed precision (see serving.paced)"}
     if rank != 0:
         return
     cpu = None
@@ -623,6 +629,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=4.0,
                     help="oracle seconds per timed step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="next_rows,gradient,macrocycle,water,serving",
+                    help="comma-separated measurements beside the headline")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the measurements beside the headline (gradient, 445-AO macrocycle, "
                          "next rows, 25-AO FP64 request, serving stream)")

@@ -281,8 +281,7 @@ int launch_class(const DevProgs &PR, const ClassLaunch &cl_in, const JobTable &T
   if (smem > (size_t)kMaxSmem)
     return set_error(LTJK_EUNSUPPORTED, "class (%d%d|%d%d) needs %zu bytes of shared memory",
                      cl.p.la, cl.p.lb, cl.p.lc, cl.p.ld, smem);
-  const int ctas_needed = (T.total + cl.warps - 1) / cl.warps;
-  const int grid = std::min(ctas_needed, num_sms() * 32);
+  const int grid = (T.total + cl.warps - 1) / cl.warps;  // one warp per item, not persistent
   quartet_kernel<Real, MODE><<<grid, 32 * cl.warps, smem, st>>>(PR, cl, T);
   CUDA_TRY(cudaGetLastError());
   g_launches += 1;
@@ -290,7 +289,7 @@ int launch_class(const DevProgs &PR, const ClassLaunch &cl_in, const JobTable &T
 }
 
 // Class-specialised J/K kernel of class (LA LB|LC LD): four warps per CTA, a
-// persistent grid of as many CTAs as fit on the device at once.
+// CTA per four work items.
 template <typename Real, int LA, int LB, int LC, int LD>
 int launch_gen_cls(const JobTable &T, cudaStream_t st) {
   if (T.total <= 0) return LTJK_OK;
@@ -298,16 +297,17 @@ int launch_gen_cls(const JobTable &T, cudaStream_t st) {
   constexpr int NACC = kGenSmemAcc<LA, LB, LC, LD> ? GenClass<LA, LB, LC, LD>::kAcc : 0;
   constexpr int kWarps = 4;
   const size_t smem = gen_warp_smem<NOUT, NACC, Real>() * kWarps;
-  static std::atomic<int> ctas_per_sm{0};  // per instantiation
+  static std::atomic<int> configured{0};  // per instantiation
   auto kern = gen_jk_kernel<Real, LA, LB, LC, LD>;
-  if (ctas_per_sm.load() == 0) {
+  if (configured.load() == 0) {
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int n = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * kWarps, smem));
-    ctas_per_sm.store(std::max(n, 1));
+    configured.store(1);
   }
-  const int ctas_needed = (T.total + kWarps - 1) / kWarps;
-  const int grid = std::min(ctas_needed, num_sms() * ctas_per_sm.load());
+  // one warp per work item, no persistent CTAs: each CTA retires after its
+  // items, so SMs turn over every few hundred microseconds and concurrent
+  // launches (other classes, higher-priority streams of the service) get
+  // them without waiting for this launch to end
+  const int grid = (T.total + kWarps - 1) / kWarps;
   kern<<<grid, 32 * kWarps, smem, st>>>(T);
   CUDA_TRY(cudaGetLastError());
   g_launches += 1;
@@ -860,7 +860,16 @@ int ltjk_context_create(const ltjk_basis *bs, const ltjk_opts *opts, ltjk_ctx **
     DevBuf d_out;
     if ((rc = d_out.alloc(sizeof(double) * std::max<long long>(total, 1)))) return rc;
     std::vector<long long> offs;
-    if ((rc = store_blocks(*c, qs, LTJK_FP64_NATIVE, offs, d_out.as<double>(), 0))) return rc;
+    // on a private highest-priority stream: a context created while other
+    // work runs (a serving frontend) does not wait behind that work's blocks
+    int plo = 0, phi = 0;
+    CUDA_TRY(cudaDeviceGetStreamPriorityRange(&plo, &phi));
+    cudaStream_t cst = nullptr;
+    CUDA_TRY(cudaStreamCreateWithPriority(&cst, cudaStreamNonBlocking, phi));
+    rc = store_blocks(*c, qs, LTJK_FP64_NATIVE, offs, d_out.as<double>(), cst);
+    cudaStreamSynchronize(cst);
+    cudaStreamDestroy(cst);
+    if (rc) return rc;
     std::vector<double> blocks(total);
     CUDA_TRY(cudaMemcpy(blocks.data(), d_out.p, sizeof(double) * total, cudaMemcpyDeviceToHost));
     c->pair_Q.assign(c->npairs, 0.0);

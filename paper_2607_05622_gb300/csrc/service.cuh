@@ -31,6 +31,15 @@ struct SvcJob {
   JKArgs a{};
   double *Jq = nullptr, *Kq = nullptr;
   const double *scale = nullptr;  // per-density scales of the prologue
+  int lane = 0;                   // stream set: 0 bulk, 1 fast (small requests)
+};
+
+// One set of streams: a prologue/epilogue stream and the side streams its
+// class launches run on (fork before a step, join before an epilogue).
+struct StreamSet {
+  cudaStream_t st = nullptr;
+  cudaStream_t side[kSideStreams] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
 };
 
 double now_s() {
@@ -41,9 +50,15 @@ double now_s() {
 
 struct ltjk_service {
   int device = 0;
-  cudaStream_t st = nullptr;
-  cudaStream_t side[kSideStreams] = {};  // class launches of a step run concurrently
-  cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
+  // Two stream sets: bulk (lowest priority) for large requests, which advance
+  // step_items work items per class per step, and fast (highest priority) for
+  // requests of at most kFastFlops algorithmic flops (about 10 ms of work
+  // alone), which issue all their work in one step.  The block scheduler starts the fast set's CTAs ahead of the
+  // bulk set's pending ones, and a fast request's epilogue joins only the
+  // fast streams, so a small request does not queue behind the steps already
+  // issued for large ones.
+  StreamSet set[2];
+  static constexpr double kFastFlops = 2e10;
   Arena arena;
   std::thread thr;
   std::mutex mu;
@@ -54,7 +69,12 @@ struct ltjk_service {
   uint64_t next_ticket = 1;
   bool stop = false;
   int fail_next_admission = 0;
-  int step_items = 2048;  // work items per request per class per step
+  // work items per request per class per step, and steps queued on the
+  // device ahead of the host: a request that arrives waits for the steps
+  // already queued, so both bound its first-step delay (2048 and 8 let a
+  // small request behind a large one wait up to 70x its own service time)
+  int step_items = 1024;
+  static constexpr int kRunAhead = kSideStreams;
   // statistics
   std::vector<double> lat;
   uint64_t submitted = 0, completed = 0, cancelled = 0, failed = 0, steps = 0, launches = 0;
@@ -76,7 +96,7 @@ struct ltjk_service {
     if (e) event_pool.push_back(e);
   }
   void run();
-  int step(std::vector<SvcJob *> &run_jobs);
+  int step(std::vector<SvcJob *> &run_jobs, const StreamSet &S, int cap);
 };
 
 namespace {
@@ -102,9 +122,10 @@ int wait_event(cudaEvent_t e, double timeout_s) {
 
 }  // namespace
 
-// One step: per (precision, mode, quartet class) one launch over the next chunk
-// of every runnable job.  Returns the number of launches.
-int ltjk_service::step(std::vector<SvcJob *> &run) {
+// One step of one stream set: per (precision, mode, quartet class) one launch
+// over the next chunk (at most cap items per job; cap 0: all remaining) of
+// every runnable job of the set.  Returns the number of launches.
+int ltjk_service::step(std::vector<SvcJob *> &run, const StreamSet &S, int cap) {
   const ProgramSet *ps;
   if (program_set(&ps)) return -1;
   int nl = 0;
@@ -121,7 +142,7 @@ int ltjk_service::step(std::vector<SvcJob *> &run) {
           // a class always runs on the same side stream: launches of one class
           // stay ordered, different classes overlap, and no step waits for
           // the previous one to drain
-          cudaStream_t st = side[q % kSideStreams];
+          cudaStream_t st = S.side[q % kSideStreams];
           if (mode == 0) {
             if (prec == 0)
               launch_jk<dflt>(*prog, PR, T, st);
@@ -152,7 +173,7 @@ int ltjk_service::step(std::vector<SvcJob *> &run) {
             int &cur = prec != 1 ? j->cur64[w] : j->cur32[w];
             const int n = prec != 1 ? cw.n64 : cw.n32;
             if (cur >= n) continue;
-            const int take = std::min(step_items, n - cur);
+            const int take = cap > 0 ? std::min(cap, n - cur) : n - cur;
             prog = &ps->progs[quartet_index(cw.la, cw.lb, cw.lc, cw.ld, mode)];
             JobDesc &D = T.j[T.njobs++];
             D.B = c->basis();
@@ -219,6 +240,13 @@ void ltjk_service::run() {
       const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16);
       j->cur64.assign(c->work.size(), 0);
       j->cur32.assign(c->work.size(), 0);
+      // small requests by the flop model (item counts say little: small
+      // molecules get one ket per work item)
+      const double work = j->req.kind == LTJK_REQ_JK
+                              ? c->stats.eri_flops_per_build + 20.0 * c->stats.cart_integrals_kept * j->req.n
+                              : c->stats.grad_eri_flops + c->stats.cart_integrals_kept * (2.0 * j->req.n + 18.0);
+      j->lane = work <= kFastFlops ? 1 : 0;
+      cudaStream_t st = set[j->lane].st;
       JKArgs a{};
       if (j->req.kind == LTJK_REQ_JK) {
         if (jk_prologue(c, j->req.D, mem, j->req.n, j->req.J != nullptr, j->req.K != nullptr, st, &a) != LTJK_OK)
@@ -240,12 +268,28 @@ void ltjk_service::run() {
       launches += 2;
       run_jobs.push_back(j);
     }
-    if (!admitted.empty()) {  // their layout copies (on st) precede their class launches
-      cudaEventRecord(fork_ev, st);
-      for (int k = 0; k < kSideStreams; ++k) cudaStreamWaitEvent(side[k], fork_ev, 0);
+    for (int l = 0; l < 2; ++l) {  // their layout copies (on st) precede their class launches
+      bool any = false;
+      for (SvcJob *j : admitted) any |= j->lane == l;
+      if (!any) continue;
+      cudaEventRecord(set[l].fork_ev, set[l].st);
+      for (int k = 0; k < kSideStreams; ++k) cudaStreamWaitEvent(set[l].side[k], set[l].fork_ev, 0);
     }
-    int nl = 0;
-    if (!run_jobs.empty()) nl = step(run_jobs);
+    // bulk steps run at most kRunAhead ahead of the device; the check never
+    // blocks, so admission, fast requests and completions keep moving while
+    // the bulk queue is full
+    while (!inflight.empty() && cudaEventQuery(inflight.front()) != cudaErrorNotReady) {
+      put_event(inflight.front());
+      inflight.pop_front();
+    }
+    const bool bulk_ok = inflight.size() < (size_t)kRunAhead;
+    int nl = 0, nl_bulk = 0;
+    {
+      std::vector<SvcJob *> part[2];
+      for (SvcJob *j : run_jobs) part[j->lane].push_back(j);
+      if (!part[1].empty()) nl += step(part[1], set[1], 0);
+      if (!part[0].empty() && bulk_ok) nl += (nl_bulk = step(part[0], set[0], step_items));
+    }
     if (nl > 0) {
       ++steps;
       launches += nl;
@@ -265,13 +309,17 @@ void ltjk_service::run() {
         if (all) to_finish.push_back(j);
       }
     }
-    if (!to_finish.empty()) {  // every class launch issued so far precedes the epilogues
+    for (int l = 0; l < 2; ++l) {  // the set's class launches so far precede its epilogues
+      bool any = false;
+      for (SvcJob *j : to_finish) any |= j->lane == l;
+      if (!any) continue;
       for (int k = 0; k < kSideStreams; ++k) {
-        cudaEventRecord(join_ev[k], side[k]);
-        cudaStreamWaitEvent(st, join_ev[k], 0);
+        cudaEventRecord(set[l].join_ev[k], set[l].side[k]);
+        cudaStreamWaitEvent(set[l].st, set[l].join_ev[k], 0);
       }
     }
     for (SvcJob *j : to_finish) {
+      cudaStream_t st = set[j->lane].st;
       if (!j->cancel_req && j->req.kind == LTJK_REQ_JK) {
         ltjk_ctx *c = j->req.ctx;
         const size_t n = (size_t)c->nao * c->nao * j->req.n;
@@ -285,17 +333,14 @@ void ltjk_service::run() {
       std::lock_guard<std::mutex> g(mu);
       j->state = kDraining;
     }
-    // keep the host a bounded number of steps ahead of the device
-    if (nl > 0) {
+    // keep the host a bounded number of bulk steps ahead of the device
+    if (nl_bulk > 0) {
       cudaEvent_t se = get_event();
-      cudaEventRecord(se, side[steps % kSideStreams]);
+      cudaEventRecord(se, set[0].side[steps % kSideStreams]);
       inflight.push_back(se);
     }
-    while (inflight.size() > 2 * kSideStreams) {
-      wait_event(inflight.front(), 600.0);
-      put_event(inflight.front());
-      inflight.pop_front();
-    }
+    if (nl == 0 && to_finish.empty() && admitted.empty())
+      std::this_thread::sleep_for(std::chrono::microseconds(50));  // waiting on the device
     // completions
     {
       std::lock_guard<std::mutex> g(mu);
@@ -353,12 +398,18 @@ int ltjk_service_create(size_t hbm_budget_bytes, int device, ltjk_service **out)
   cudaError_t e = cudaMalloc(&p, hbm_budget_bytes);
   if (e != cudaSuccess) return set_error(LTJK_ENOMEM, "service arena of %zu bytes: %s", hbm_budget_bytes, cudaGetErrorString(e));
   s->arena.init(static_cast<char *>(p), hbm_budget_bytes);
-  e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
-  for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) {
-    e = cudaStreamCreateWithFlags(&s->side[k], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join_ev[k], cudaEventDisableTiming);
+  int prio_low = 0, prio_high = 0;
+  e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  for (int l = 0; l < 2 && e == cudaSuccess; ++l) {
+    StreamSet &S = s->set[l];
+    const int prio = l == 1 ? prio_high : prio_low;
+    e = cudaStreamCreateWithPriority(&S.st, cudaStreamNonBlocking, prio);
+    for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) {
+      e = cudaStreamCreateWithPriority(&S.side[k], cudaStreamNonBlocking, prio);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.join_ev[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.fork_ev, cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaFree(p);
     return set_error(LTJK_ECUDA, "stream: %s", cudaGetErrorString(e));
@@ -488,16 +539,20 @@ int ltjk_service_destroy(ltjk_service *s) {
   }
   if (s->thr.joinable()) s->thr.join();
   cudaSetDevice(s->device);
-  cudaStreamSynchronize(s->st);
+  for (int l = 0; l < 2; ++l)
+    if (s->set[l].st) cudaStreamSynchronize(s->set[l].st);
   for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
   for (auto &kv : s->jobs)
     if (kv.second->ev) cudaEventDestroy(kv.second->ev);
-  for (int k = 0; k < kSideStreams; ++k) {
-    if (s->side[k]) cudaStreamDestroy(s->side[k]);
-    if (s->join_ev[k]) cudaEventDestroy(s->join_ev[k]);
+  for (int l = 0; l < 2; ++l) {
+    StreamSet &S = s->set[l];
+    for (int k = 0; k < kSideStreams; ++k) {
+      if (S.side[k]) cudaStreamDestroy(S.side[k]);
+      if (S.join_ev[k]) cudaEventDestroy(S.join_ev[k]);
+    }
+    if (S.fork_ev) cudaEventDestroy(S.fork_ev);
+    if (S.st) cudaStreamDestroy(S.st);
   }
-  if (s->fork_ev) cudaEventDestroy(s->fork_ev);
-  cudaStreamDestroy(s->st);
   cudaFree(s->arena.base);
   delete s;
   return LTJK_OK;

@@ -68,9 +68,10 @@ def run_stream(L, torch, dev, nreq=256, nao_hi=730, budget_gb=150.0, load=0.8, f
     saturated: every request arrives at time 0 (offered load above capacity),
     so the throughput measured is the service's capacity, not the arrival rate."""
     reqs = W.serving_requests(nreq, seed=seed, nao_hi=nao_hi, rate_hz=1.0)
-    # untimed warm-up: load every kernel and table the passes below use
+    # untimed warm-up over the whole list: load every kernel and table the
+    # passes below use (first launches would otherwise land in pass 1)
     for prec in (L.FP64_NATIVE, L.MIXED):
-        for r in reqs[:4]:
+        for r in reqs:
             ctx, inp = prepare(L, r, prec, dev, torch)
             if r["kind"] == "jk":
                 ctx.jk_build(inp["D"])
@@ -125,7 +126,8 @@ def run_stream(L, torch, dev, nreq=256, nao_hi=730, budget_gb=150.0, load=0.8, f
     svc = L.Service(int(budget_gb * (1 << 30)))
     pending = {}
     lock = threading.Lock()
-    lat, errs_j, errs_k, errs_g = [], [], [], []
+    lat, slow, errs_j, errs_k, errs_g, per_req = [], [], [], [], [], []
+    t_sub = {}
     t_start = time.perf_counter()
 
     def arrive(i):
@@ -133,7 +135,7 @@ def run_stream(L, torch, dev, nreq=256, nao_hi=730, budget_gb=150.0, load=0.8, f
         if dt > 0:
             time.sleep(dt)
         r = reqs[i]
-        s_ = torch.cuda.Stream()
+        s_ = torch.cuda.Stream(priority=-1)  # the frontend's work ahead of queued bulk steps
         with torch.cuda.stream(s_):
             ctx, inp = prepare(L, r, L.MIXED, dev, torch)
             if r["kind"] == "jk":
@@ -144,8 +146,14 @@ def run_stream(L, torch, dev, nreq=256, nao_hi=730, budget_gb=150.0, load=0.8, f
                 out = (g,)
         with lock:
             pending[tk] = (i, ctx, inp, out, arrivals[i])
+            t_sub[i] = time.perf_counter() - t_start
+
+    done_list = []
 
     def harvest():
+        # completion times only: the checks against the FP64 results (device
+        # gathers and copies that would queue behind the running work and
+        # delay the next timestamps) run after the stream
         with lock:
             items = list(pending.items())
         for tk, (i, ctx, inp, out, t_arr) in items:
@@ -155,15 +163,9 @@ def run_stream(L, torch, dev, nreq=256, nao_hi=730, budget_gb=150.0, load=0.8, f
             t_done = time.perf_counter() - t_start
             L._check(rc)
             lat.append(t_done - t_arr)
-            if reqs[i]["kind"] == "jk":
-                J, K = out
-                rj, rk, mj, mk, idx = ref[i]
-                errs_j.append(float(np.abs(J.flatten()[idx].cpu().numpy() - rj).max()) / mj)
-                errs_k.append(float(np.abs(K.flatten()[idx].cpu().numpy() - rk).max()) / mk)
-            else:
-                g = out[0].cpu().numpy()
-                errs_g.append(float(np.abs(g - ref[i][0]).max() / np.abs(ref[i][0]).max()))
-            ctx.close()
+            slow.append((t_done - t_arr) / seq_mixed[i])
+            per_req.append((slow[-1], i, t_arr, t_done))
+            done_list.append((i, ctx, out))
             with lock:
                 del pending[tk]
 
@@ -178,8 +180,21 @@ def run_stream(L, torch, dev, nreq=256, nao_hi=730, budget_gb=150.0, load=0.8, f
     span = time.perf_counter() - t_start
     st = svc.stats()
     svc.close()
+    torch.cuda.synchronize()
+    for i, ctx, out in done_list:
+        if reqs[i]["kind"] == "jk":
+            J, K = out
+            rj, rk, mj, mk, idx = ref[i]
+            errs_j.append(float(np.abs(J.flatten()[idx].cpu().numpy() - rj).max()) / mj)
+            errs_k.append(float(np.abs(K.flatten()[idx].cpu().numpy() - rk).max()) / mk)
+        else:
+            g = out[0].cpu().numpy()
+            errs_g.append(float(np.abs(g - ref[i][0]).max() / np.abs(ref[i][0]).max()))
+        ctx.close()
     lat_ms = sorted(1e3 * x for x in lat)
     pct = lambda p: lat_ms[min(len(lat_ms) - 1, int(round(p * (len(lat_ms) - 1))))]  # noqa: E731
+    slow_s = sorted(slow)
+    spct = lambda p: slow_s[min(len(slow_s) - 1, int(round(p * (len(slow_s) - 1))))]  # noqa: E731
     nao = [r["mol"].nao for r in reqs]
     return {
         "metric": "serving: p50/p99 latency and throughput, mixed precision, continuous batching",
@@ -189,6 +204,12 @@ def run_stream(L, torch, dev, nreq=256, nao_hi=730, budget_gb=150.0, load=0.8, f
         "arrivals": "all at t = 0 (saturated)" if saturated else f"Poisson at {load} x capacity",
         "arrival_rate_hz": None if saturated else rate, "offered_load": None if saturated else load,
         "p50_ms": pct(0.5), "p99_ms": pct(0.99), "mean_ms": statistics.mean(lat_ms),
+        "slowdown_p50": spct(0.5), "slowdown_p99": spct(0.99),
+        "slowdown_what": "latency / the request's stand-alone mixed service time (same list, one at a time)",
+        "worst_slowdowns": [{"nao": reqs[i]["mol"].nao, "kind": reqs[i]["kind"], "arrival_s": round(ta, 3),
+                             "latency_ms": round(1e3 * (td - ta), 1), "alone_ms": round(1e3 * seq_mixed[i], 1),
+                             "frontend_ms": round(1e3 * (t_sub[i] - ta), 1)}
+                            for sl, i, ta, td in sorted(per_req, key=lambda x: -x[0])[:5]],
         "throughput_rps": len(reqs) / span, "span_s": span,
         "sequential_fp64": {"throughput_rps": len(reqs) / sum(seq_fp64),
                             "p50_service_ms": 1e3 * float(np.median(seq_fp64)),
@@ -198,7 +219,10 @@ def run_stream(L, torch, dev, nreq=256, nao_hi=730, budget_gb=150.0, load=0.8, f
                           "K_max_rel_to_max": max(errs_k) if errs_k else None,
                           "grad_max_rel_to_max": max(errs_g) if errs_g else None,
                           "how": "4096 sampled elements per J/K result, full gradient"},
-        "service": {k2: st[k2] for k2 in ("steps", "launches", "bytes_peak", "budget", "completed")},
+        "service": {k2: st[k2] for k2 in ("steps", "launches", "bytes_peak", "budget", "completed",
+                                          "p50_ms", "p99_ms")},
+        "service_latency_what": "service p50/p99: submission to completion inside the service (without "
+                                "the frontend's context creation and density formation)",
         "budget_gb": budget_gb, "frontend_threads": frontend_threads,
     }
 

@@ -105,3 +105,36 @@ def test_budget_admission_and_faults(L):
     with pytest.raises(L.LtjkError):
         svc.wait(987654, 0.0)
     svc.close()
+
+
+def test_request_admitted_while_another_runs(L):
+    """Continuous batching, not a queue: a small request submitted while a
+    large one's kernels are already on the device is admitted into the
+    running steps and completes first; both equal their stand-alone builds."""
+    w = W.config3()  # 445 AO: many more work items (so steps) than the scheduler runs ahead
+    big = L.Context(w.mol, schwarz_tau=1e-12, precision=L.MIXED)
+    Db = dev(np.random.default_rng(7).standard_normal((8, w.mol.nao, w.mol.nao)))
+    Jb0, Kb0 = big.jk_build(Db)
+    m = molecules()[0]
+    small = L.Context(m, schwarz_tau=1e-12, precision=L.MIXED)
+    Ds = dev(np.random.default_rng(8).standard_normal((4, m.nao, m.nao)))
+    Js0, Ks0 = small.jk_build(Ds)
+    torch.cuda.synchronize()
+    svc = L.Service(1 << 32)
+    tb, Jb, Kb = svc.submit_jk(big, Db)
+    # wait until the large request is admitted and its first steps are launched
+    import time
+    t0 = time.time()
+    while svc.stats()["steps"] < 1 and time.time() - t0 < 30:
+        time.sleep(0.0005)
+    done_b, _ = svc.poll(tb)
+    st = svc.stats()
+    assert not done_b and st["active"] >= 1
+    ts, Js, Ks = svc.submit_jk(small, Ds)
+    svc.wait(ts, 120)
+    done_b_at_small, _ = svc.poll(tb)
+    svc.wait(tb, 120)
+    assert not done_b_at_small  # the small one did not wait for the large one
+    assert rel(Js, Js0) < TOL and rel(Ks, Ks0) < TOL
+    assert rel(Jb, Jb0) < TOL and rel(Kb, Kb0) < TOL
+    svc.close()
