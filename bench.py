@@ -371,6 +371,44 @@ def measure_macrocycle(ltjk, torch, dev, local, stream, reps=2):
     return out
 
 
+def measure_fshell(ltjk, torch, dev, local, stream, reps=3):
+    """J/K of 48 pseudo-densities on the 200-AO f-shell chain (4 heavy atoms
+    4s3p2d1f, 4 H 3s2p1d; every class up to (ff|ff)): builds/s in the FP64
+    class, mixed and IEEE FP64 modes, and the FP64-class and mixed error
+    against the IEEE FP64 build on the same GPU (all three parity-tested
+    against the oracle on the smaller f-shell molecules)."""
+    w = W.config_fshell()
+    mol = w.mol
+    xmin = 2.0 * (w.eps_vir.min() - w.eps_occ.max())
+    xmax = 2.0 * (w.eps_vir.max() - w.eps_occ.min())
+    tq, _, _ = ltjk.laplace_quadrature(xmin, xmax, w.nlap)
+    out = {"workload": w.name, "nao": mol.nao, "ndens": w.ndens}
+    res = {}
+    for name, prec, r in (("fp64_class", ltjk.FP64, reps), ("mixed", ltjk.MIXED, reps),
+                          ("fp64_native", ltjk.FP64_NATIVE, 1)):
+        t0 = time.perf_counter()
+        c = ltjk.Context(mol, schwarz_tau=w.schwarz_tau, mixed_tau=1e-6, precision=prec, device=local)
+        setup_s = time.perf_counter() - t0
+        D = c.pseudo_densities(torch.from_numpy(w.C_occ).to(dev), torch.from_numpy(w.C_vir).to(dev),
+                               torch.from_numpy(w.eps_occ).to(dev), torch.from_numpy(w.eps_vir).to(dev),
+                               torch.from_numpy(np.ascontiguousarray(w.X)).to(dev), tq)
+        J, K = c.jk_build(D)
+        ms = _event_ms(torch, stream, lambda: c.jk_build(D, J, K), r)
+        st = c.stats()
+        out[name] = {"build_ms": ms, "builds_per_s": w.ndens / (ms / 1e3), "setup_ms": 1e3 * setup_s,
+                     "quartets_kept": st["quartets_kept"], "quartets_fp64": st["quartets_fp64"],
+                     "quartets_per_s": st["quartets_kept"] / (ms / 1e3)}
+        res[name] = (J, K)
+        del c, D
+    J64, K64 = res["fp64_native"]
+    for name in ("fp64_class", "mixed"):
+        J, K = res[name]
+        out[name]["error_vs_fp64"] = {"J_max_rel_to_max": float((J - J64).abs().max() / J64.abs().max()),
+                                      "K_max_rel_to_max": float((K - K64).abs().max() / K64.abs().max())}
+    del res, J64, K64
+    return out
+
+
 def measure_next_rows(ltjk, torch, stream, ctx, w, J, K, Co, Cv, xmin, xmax, peaks, reps=5):
     """The rows either side of the build: the Laplace-Fock back-transform of the
     48 J/K pairs to the occupied-virtual block (Eq. laplacefock; FP64 GEMMs on
@@ -579,6 +617,8 @@ def run_gpu(args, world, rank, local):
             extras["macrocycle_445"] = measure_macrocycle(ltjk, torch, dev, local, stream)
         if "water" in legs:
             extras["water_fp64_single_request"] = measure_config1(ltjk, torch, dev, local, stream)
+        if "fshell" in legs:
+            extras["fshell_chain_200"] = measure_fshell(ltjk, torch, dev, local, stream)
         if "serving" in legs:
             extras["serving"] = measure_serving(ltjk, torch, dev)
             pc = extras["serving"]["paced"]
@@ -629,11 +669,11 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=4.0,
                     help="oracle seconds per timed step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="next_rows,gradient,macrocycle,water,serving",
+    ap.add_argument("--legs", default="next_rows,gradient,macrocycle,water,fshell,serving",
                     help="comma-separated measurements beside the headline")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the measurements beside the headline (gradient, 445-AO macrocycle, "
-                         "next rows, 25-AO FP64 request, serving stream)")
+                         "next rows, 25-AO FP64 request, 200-AO f-shell chain, serving stream)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -45,13 +45,14 @@ extern "C" {
 #define LTJK_EINVAL (-1)        /* invalid argument (null pointer, bad size, bad basis) */
 #define LTJK_ENOMEM (-2)        /* device or host allocation failed */
 #define LTJK_EBUDGET (-3)       /* request does not fit the service's HBM budget */
-#define LTJK_EUNSUPPORTED (-4)  /* angular momentum above the compiled maximum */
+#define LTJK_EUNSUPPORTED (-4)  /* angular momentum above the compiled maximum of the call */
 #define LTJK_ECUDA (-5)         /* a CUDA runtime call failed */
 #define LTJK_ETIMEDOUT (-6)     /* a bounded wait ran out */
 #define LTJK_ECANCELLED (-7)    /* the request was cancelled */
 #define LTJK_ENOTREADY (-8)     /* result not yet available */
 
-#define LTJK_MAX_L 2            /* largest shell angular momentum of the value build */
+#define LTJK_MAX_L 3            /* largest shell angular momentum of the J/K build (s, p, d, f) */
+#define LTJK_MAX_L_GRAD 2       /* largest shell angular momentum of the gradient adjoint */
 #define LTJK_MAX_PRIM 8         /* largest number of primitives in one shell */
 
 #define LTJK_FP64 0         /* FP64-class: double-float recurrences and digestion */
@@ -281,7 +282,11 @@ int ltjk_jk_energy(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, 
    integrals for three centres, the fourth by translational invariance
    (Eq. l18).  Only the two-electron term: no one-electron or nuclear part.
      P, Q [nterms][N][N] (device, any symmetry), grad [natoms][3] (device,
-     overwritten).  1 <= nterms <= 4096. */
+     overwritten).  1 <= nterms <= 4096.  Shells up to LTJK_MAX_L_GRAD (d):
+     a context with an f shell gives LTJK_EUNSUPPORTED before any launch (the
+     derivative programs of f quartets need one more unit, g, and their
+     contracted accumulators alone, 29340 of them for (ff|ff), exceed a
+     warp's shared memory). */
 int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, double cJ,
                  double cK, double *grad, ltjk_stream stream);
 
@@ -314,8 +319,10 @@ int ltjk_alu_peak(int kind, double *flops, ltjk_stream stream);
    in Cartesian shells (Computational Details); this maps AO matrices to real
    spherical functions, T block diagonal over the shells: s 1; p x, y, z (the
    Cartesian order); d, m = -2..2: sqrt3 xy, sqrt3 yz, (2 zz - xx - yy)/2,
-   sqrt3 xz, sqrt3 (xx - yy)/2, with every Cartesian component normalised as
-   x^l.  direction 0: B[q] = T A[q] T^T (A [ndens][N][N] Cartesian, e.g. J
+   sqrt3 xz, sqrt3 (xx - yy)/2; f, m = -3..3: sqrt(5/8) y(3xx - yy),
+   sqrt15 xyz, sqrt(3/8) y(4zz - xx - yy), z(2zz - 3xx - 3yy)/2,
+   sqrt(3/8) x(4zz - xx - yy), sqrt15/2 z(xx - yy), sqrt(5/8) x(xx - 3yy);
+   with every Cartesian component normalised as x^l.  direction 0: B[q] = T A[q] T^T (A [ndens][N][N] Cartesian, e.g. J
    or K, to B [ndens][Ns][Ns]); direction 1: B[q] = T^T A[q] T (a spherical
    density A [ndens][Ns][Ns] to the Cartesian B [ndens][N][N] the build
    takes).  IEEE FP64, device arrays; uses the context's scratch.
@@ -386,14 +393,21 @@ int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int preci
    recurrence level writes a slot that the same level reads, so the lanes of a
    warp can run a level's steps in any order).  Host-only, no device needed.
      0 <= la, lb, lc, ld <= LTJK_MAX_L; deriv 0 (integrals) or 1 (derivative
-     integrals, one extra unit of angular momentum); *out is overwritten.
-   LTJK_EUNSUPPORTED for l above LTJK_MAX_L, LTJK_EINVAL for a null out. */
+     integrals, one extra unit of angular momentum; l up to LTJK_MAX_L_GRAD);
+     *out is overwritten.  The integrals of the heavier value classes are
+     produced in output tiles over the first index (a range of a's Cartesian
+     components per tile), so that a tile's horizontal recurrence fits the
+     warp's shared memory; derivative classes have nine tiles, one per
+     (centre, direction).
+   LTJK_EUNSUPPORTED for l above LTJK_MAX_L (LTJK_MAX_L_GRAD with deriv = 1),
+   LTJK_EINVAL for a null out. */
 typedef struct {
   int ltot;              /* la+lb+lc+ld (+1 for derivatives) */
   int vrr_steps, vrr_levels, vrr_slots;   /* vertical recurrence per primitive quartet */
   int accumulators;      /* contracted [e0|f0] values, all channels */
   int hrr_steps, hrr_levels, hrr_slots;   /* horizontal recurrence, largest output tile */
-  int tiles, outputs;    /* output tiles and integrals per tile (na nb nc nd) */
+  int tiles, outputs;    /* output tiles; integrals of the largest tile (na nb nc nd
+                            when the class has one value tile or is a derivative) */
   double vrr_flops;      /* flop model per primitive quartet (recurrence only) */
   double hrr_flops;      /* flop model per contracted quartet */
   size_t smem_per_warp[3]; /* bytes per warp: IEEE FP64, double-float, FP32 */
@@ -441,7 +455,8 @@ typedef struct {
 
 /* Create a service with an HBM budget (bytes, >= 1 MiB, allocated now) on a device. */
 int ltjk_service_create(size_t hbm_budget_bytes, int device, ltjk_service **out);
-/* Queue a request; *ticket identifies it.  LTJK_EBUDGET if it can never fit. */
+/* Queue a request; *ticket identifies it.  LTJK_EBUDGET if it can never fit;
+   LTJK_EUNSUPPORTED for a gradient request on a context with an f shell. */
 int ltjk_service_submit(ltjk_service *svc, const ltjk_request *req, uint64_t *ticket);
 /* Non-blocking: *done = 1 once finished; then returns the request's status. */
 int ltjk_service_poll(ltjk_service *svc, uint64_t ticket, int *done);

@@ -172,9 +172,9 @@ int device_programs(int dev, DevProgs *out, const double **boys, const float2 **
     auto b2 = std::make_shared<DevBuf>();
     if ((rc = b2->upload(tab2))) return rc;
     g_prog.boys2[dev] = b2;
-    double inv_odd[kBoysRaw + 2], half_n[2 * kMaxLDeriv + 4];
+    double inv_odd[kBoysRaw + 2], half_n[kNhMax];
     for (int m = 0; m < kBoysRaw + 2; ++m) inv_odd[m] = 1.0 / (2 * m + 1);
-    for (int n = 0; n < 2 * kMaxLDeriv + 4; ++n) half_n[n] = 0.5 * n;
+    for (int n = 0; n < kNhMax; ++n) half_n[n] = 0.5 * n;
     CUDA_TRY(cudaMemcpyToSymbol(c_inv_odd, inv_odd, sizeof(inv_odd)));
     CUDA_TRY(cudaMemcpyToSymbol(c_half_n, half_n, sizeof(half_n)));
     g_prog.vrr[dev] = v;
@@ -217,7 +217,7 @@ ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
     cl.T = 32;
     cl.smem_per_warp = (int)warp_smem_bytes(p, cl.G, cl.T, real_bytes);
     while (cl.T > 8 && cl.T / 2 >= cl.G && cl.smem_per_warp > kSmemPerSM / 16 &&
-           (size_t)(cl.T / 2) * pt_stride(p) * real_bytes >= (size_t)kDigestTableBytes) {
+           (size_t)(cl.T / 2) * pt_stride(p) * real_bytes >= digest_table_bytes(p)) {
       cl.T /= 2;
       cl.smem_per_warp = (int)warp_smem_bytes(p, cl.G, cl.T, real_bytes);
     }
@@ -494,7 +494,7 @@ int store_blocks(ltjk_ctx &c, const std::vector<std::pair<int, int>> &qs, int pr
     const int qi = quartet_index(c.sh_l[ab.x], c.sh_l[ab.y], c.sh_l[cd.x], c.sh_l[cd.y], 0);
     by_class[qi].push_back((int)k);
     offsets[k] = off;
-    off += (long long)ps->progs[qi].nout * ps->progs[qi].ntile;
+    off += ps->progs[qi].nout;  // the whole value block, its tiles at their own offsets
   }
   DevBasis B = c.basis();
   for (auto &kv : by_class) {
@@ -954,7 +954,7 @@ int ltjk_sph_transform(ltjk_ctx *ctx, int direction, int ndens, const double *A,
   if (ctx->nsph == 0) {
     // T, block diagonal: real solid harmonics of each shell in terms of its
     // Cartesian components (every component normalised as x^l); p keeps the
-    // Cartesian order x, y, z; d in the order m = -2..2.
+    // Cartesian order x, y, z; d and f in the order m = -l..l.
     int Ns = 0;
     for (int l : ctx->sh_l) Ns += 2 * l + 1;
     std::vector<double> T((size_t)Ns * Nc, 0.0);
@@ -976,6 +976,30 @@ int ltjk_sph_transform(ltjk_ctx *ctx, int direction, int ndens, const double *A,
         at(3, 2) = r3;                   // xz
         at(4, 0) = 0.5 * r3;             // (xx - yy) sqrt3 / 2
         at(4, 3) = -0.5 * r3;
+      } else if (l == 3) {
+        // components xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz; m = -3..3:
+        //   sqrt(5/8) (3 xxy - yyy), sqrt15 xyz, sqrt(3/8) (4 yzz - xxy - yyy),
+        //   (2 zzz - 3 xxz - 3 yyz) / 2, sqrt(3/8) (4 xzz - xxx - xyy),
+        //   sqrt15 / 2 (xxz - yyz), sqrt(5/8) (xxx - 3 xyy)
+        // (each the unit-norm multiple of its harmonic polynomial, with the
+        // one-centre overlap of x^a y^b z^c normalised as x^3)
+        const double c58 = std::sqrt(5.0 / 8.0), c38 = std::sqrt(3.0 / 8.0), r15 = std::sqrt(15.0);
+        at(0, 1) = 3.0 * c58;
+        at(0, 6) = -c58;
+        at(1, 4) = r15;
+        at(2, 8) = 4.0 * c38;
+        at(2, 1) = -c38;
+        at(2, 6) = -c38;
+        at(3, 9) = 1.0;
+        at(3, 2) = -1.5;
+        at(3, 7) = -1.5;
+        at(4, 5) = 4.0 * c38;
+        at(4, 0) = -c38;
+        at(4, 3) = -c38;
+        at(5, 2) = 0.5 * r15;
+        at(5, 7) = -0.5 * r15;
+        at(6, 0) = c58;
+        at(6, 3) = -3.0 * c58;
       } else {
         return set_error(LTJK_EUNSUPPORTED, "sph_transform: l = %d", l);
       }
@@ -1124,6 +1148,10 @@ int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, do
                  double *grad, ltjk_stream stream) {
   if (!ctx || !P || !Q || !grad) return set_error(LTJK_EINVAL, "jk_grad: null argument");
   if (nterms < 1 || nterms > 4096) return set_error(LTJK_EINVAL, "jk_grad: nterms %d not in 1..4096", nterms);
+  for (int s = 0; s < ctx->nshells; ++s)
+    if (ctx->sh_l[s] > kMaxLGrad)
+      return set_error(LTJK_EUNSUPPORTED, "jk_grad: shell %d has l = %d above LTJK_MAX_L_GRAD = %d", s,
+                       ctx->sh_l[s], kMaxLGrad);
   CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t NN = (size_t)ctx->nao * ctx->nao, n = NN * nterms;
@@ -1249,9 +1277,11 @@ int ltjk_alu_peak(int kind, double *flops, ltjk_stream stream) {
 int ltjk_class_program(int la, int lb, int lc, int ld, int deriv, ltjk_program_info *out) {
   if (!out) return set_error(LTJK_EINVAL, "class_program: null argument");
   if (deriv != 0 && deriv != 1) return set_error(LTJK_EINVAL, "class_program: deriv must be 0 or 1");
+  const int lmax = deriv ? kMaxLGrad : kMaxL;
   for (int l : {la, lb, lc, ld})
-    if (l < 0 || l > kMaxL)
-      return set_error(LTJK_EUNSUPPORTED, "class_program: l = %d outside 0..%d", l, kMaxL);
+    if (l < 0 || l > lmax)
+      return set_error(LTJK_EUNSUPPORTED, "class_program: l = %d outside 0..%d%s", l, lmax,
+                       deriv ? " (derivative programs)" : "");
   const ProgramSet *ps;
   int rc = program_set(&ps);
   if (rc) return rc;
@@ -1267,9 +1297,9 @@ int ltjk_class_program(int la, int lb, int lc, int ld, int deriv, ltjk_program_i
   out->accumulators = p.acc_total;
   out->hrr_slots = p.hrr_size;
   out->tiles = p.ntile;
-  out->outputs = p.nout;
   for (int t = 0; t < p.ntile; ++t) {
     const TileProg &T = ps->tiles[p.tile_begin + t];
+    out->outputs = std::max(out->outputs, T.nout);
     const int steps = ps->levels[T.hrr_level0 + T.nhrr_level] - ps->levels[T.hrr_level0];
     out->hrr_steps = std::max(out->hrr_steps, steps);
     out->hrr_levels = std::max(out->hrr_levels, T.nhrr_level);

@@ -27,7 +27,7 @@ constexpr int kBoysM = kBoysMaxM + 1;          // orders tabulated
 constexpr int kBoysRaw = kBoysMaxM + kBoysTaylor;  // orders needed to fill the table
 
 __constant__ double c_inv_odd[kBoysRaw + 2];   // 1/(2m+1)
-__constant__ double c_half_n[2 * kMaxLDeriv + 4];  // n/2
+__constant__ double c_half_n[kNhMax];  // n/2
 
 __device__ __forceinline__ double boys_taylor(const double *__restrict__ row, double x) {
   double f = __ldg(row + kBoysTaylor - 1);
@@ -216,7 +216,6 @@ struct JobTable {
 //   [0 .. ltot]           base values [00|00]^(m)
 //   [ltot+1 .. +kNumCoef) coefficients (CoefSlot order)
 //   then hz[0..nh), he[0..nh), hs[0..nh): n/(2 zeta), n/(2 eta), n/(2(zeta+eta))
-constexpr int kNmax = 2 * kMaxLDeriv + 2;  // largest integer multiplier + 1
 __host__ __device__ inline int pt_stride(const ClassProg &p) { return p.ltot + 1 + kNumCoef + 3 * p.nh; }
 
 struct ClassLaunch {
@@ -227,12 +226,31 @@ struct ClassLaunch {
   int T;        // primitive-table entries (set-up of T primitive quartets at a time)
 };
 
+// The digestion tabulates its output offsets in the dead primitive table: ten
+// placements x ceil(nx ny / 4) groups x 4 outputs of int2, nx ny the largest
+// product of two of the quartet's component counts (at least 36, the d x d
+// table, so lighter classes keep the table they were tuned with).
+__host__ __device__ inline size_t digest_table_bytes(const ClassProg &p) {
+  int l = p.la > p.lb ? p.la : p.lb;
+  l = l > p.lc ? l : p.lc;
+  l = l > p.ld ? l : p.ld;
+  int nn = ncart(l) * ncart(l);
+  nn = nn > 36 ? nn : 36;
+  return (size_t)10 * ((nn + 3) / 4) * 4 * 8;
+}
+// Reals of the primitive table: T entries, and never less than the digestion's
+// offset table.
+__host__ __device__ inline int ptab_reals(const ClassProg &p, int T, size_t real_bytes) {
+  const int t = T * pt_stride(p);
+  const int d = (int)((digest_table_bytes(p) + real_bytes - 1) / real_bytes);
+  return t > d ? t : d;
+}
 // Shared memory one warp needs for class program p with G groups and a T-entry
 // primitive table, in bytes: primitive table, G accumulator sets and the work
 // region (Real), then for the gradient the Gamma block of one quartet (double).
 __host__ __device__ inline size_t gamma_offset(const ClassProg &p, int G, int T, size_t real_bytes) {
   int work = G * p.vrr_size > p.hrr_size ? G * p.vrr_size : p.hrr_size;
-  size_t b = (size_t)(T * pt_stride(p) + G * p.acc_total + work) * real_bytes;
+  size_t b = (size_t)(ptab_reals(p, T, real_bytes) + G * p.acc_total + work) * real_bytes;
   return (b + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t warp_smem_bytes(const ClassProg &p, int G, int T, size_t real_bytes) {
@@ -240,9 +258,6 @@ __host__ __device__ inline size_t warp_smem_bytes(const ClassProg &p, int G, int
   if (p.deriv) b += (size_t)p.nout * sizeof(double);
   return (b + 15) / 16 * 16;
 }
-// The digestion tabulates its output offsets in the dead primitive table:
-// at most 10 placements x 9 groups x 4 outputs of int2.
-constexpr int kDigestTableBytes = 10 * 9 * 4 * 8;
 
 // ------------------------------------------- stage 1: one primitive quartet
 // Base values [00|00]^(m) = 2 pi^{5/2} K_AB K_CD c.. / (zeta eta sqrt(zeta+eta))
@@ -361,8 +376,8 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
                                Real *sm, int ip, int jp, int lane) {
   const int S = 32 / G, g = lane / S, s = lane % S;
   const int stride = pt_stride(p), nh = p.nh;
-  Real *ptab = sm;                              // [T][stride]
-  Real *accs = ptab + T * stride;               // [G][acc_total]; group 0's last
+  Real *ptab = sm;                              // [T][stride] (and the digestion's table)
+  Real *accs = ptab + ptab_reals(p, T, sizeof(Real));  // [G][acc_total]; group 0's last
   Real *acc0 = accs + (G - 1) * p.acc_total;
   Real *work = acc0 + p.acc_total;              // VRR regions / HRR slots
   Real *my_acc = accs + (G - 1 - g) * p.acc_total;
@@ -556,10 +571,11 @@ __device__ __forceinline__ void digest_place(const Real *__restrict__ I, const R
   }
 }
 
-// The ten placements of one quartet.  tab is scratch shared memory of the warp
-// (its primitive table, dead between the recurrences of two kets) for the
-// per-output offsets of every placement: at most 10 x 9 groups x 4 outputs of
-// 8 bytes, kDigestTableBytes; the launch keeps the table at least that large.
+// The ten placements of one quartet (or of one output tile of it: off[0] and
+// n[0] then give the tile's range of a, and I its sub-block).  tab is scratch
+// shared memory of the warp (its primitive table, dead between the
+// recurrences of two kets) for the per-output offsets of every placement,
+// digest_table_bytes of the class; the primitive table is never smaller.
 // The output offsets x*N*nd + y*nd fit 32 bits for every size the build accepts.
 template <typename Real>
 __device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], const int n[4], int N,
@@ -687,15 +703,20 @@ __global__ void __launch_bounds__(128, 4) quartet_kernel(DevProgs PR, ClassLaunc
       if (MODE == kGrad) gamma_block(a, gam, off, n, w, N, lane);
       double g9 = 0.0;  // lane t < 9 keeps component t
       for (int tile = 0; tile < p.ntile; ++tile) {
+        const TileProg TP = PR.tiles[p.tile_begin + tile];
         const Real *I = hrr_tile<Real>(B, PR, p, tile, acc0, W.bra, jp, lane);
         if (MODE == kStore) {
-          double *o = a.out + a.out_off[li] + ((long long)kk * p.ntile + tile) * p.nout;
-          for (int t = lane; t < p.nout; t += 32) o[t] = to_double(I[t]);
+          const long long per_quartet = p.deriv ? (long long)p.ntile * p.nout : p.nout;
+          double *o = a.out + a.out_off[li] + kk * per_quartet + TP.store_off;
+          for (int t = lane; t < TP.nout; t += 32) o[t] = to_double(I[t]);
         } else if (MODE == kJK) {
           Real *Iw = const_cast<Real *>(I);
-          for (int t = lane; t < p.nout; t += 32) Iw[t] = scale_pow2(Iw[t], wf);  // degeneracy weight, once
+          for (int t = lane; t < TP.nout; t += 32) Iw[t] = scale_pow2(Iw[t], wf);  // degeneracy weight, once
           __syncwarp();
-          digest_jk<Real>(a, I, off, n, N, reinterpret_cast<int2 *>(sm), lane);
+          // the tile is the block of a "shell" made of a's components [a0, a0 + na)
+          const int offt[4] = {off[0] + TP.a0, off[1], off[2], off[3]};
+          const int nt[4] = {TP.na, n[1], n[2], n[3]};
+          digest_jk<Real>(a, I, offt, nt, N, reinterpret_cast<int2 *>(sm), lane);
         } else {
           double v = 0.0;
           for (int e = lane; e < p.nout; e += 32) v = fma(to_double(I[e]), gam[e], v);

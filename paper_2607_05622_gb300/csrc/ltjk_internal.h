@@ -8,11 +8,22 @@
 
 namespace ltjk {
 
-constexpr int kMaxL = LTJK_MAX_L;      // value build: s, p, d
-constexpr int kMaxLDeriv = kMaxL + 1;  // one raise for the derivative integrals
+constexpr int kMaxL = LTJK_MAX_L;           // value build: s, p, d, f
+constexpr int kMaxLGrad = LTJK_MAX_L_GRAD;  // gradient adjoint: s, p, d
+constexpr int kMaxLDeriv = kMaxLGrad + 1;   // one raise for the derivative integrals
 constexpr int kMaxPrim = 8;
 constexpr int kMaxPrimPair = kMaxPrim * kMaxPrim;
-constexpr int kBoysMaxM = 4 * kMaxLDeriv + 2;
+// largest total angular momentum of a quartet program, value or derivative
+constexpr int kMaxLtot = 4 * kMaxL > 4 * kMaxLGrad + 1 ? 4 * kMaxL : 4 * kMaxLGrad + 1;
+constexpr int kBoysMaxM = kMaxLtot + 2;
+// largest angular momentum on one side of a recurrence, and the integer
+// multipliers n/2 a recurrence step takes (n up to that sum, plus one)
+constexpr int kMaxSideL = 2 * kMaxL > 2 * kMaxLGrad + 1 ? 2 * kMaxL : 2 * kMaxLGrad + 1;
+constexpr int kNhMax = kMaxSideL + 2;
+// Slot budget of a value class's output tiling: accumulators plus the larger
+// of the vertical region and one tile's horizontal region (8 bytes a slot in
+// the FP64 classes: 64 KB, a quarter of an SM's shared memory).
+constexpr int kTileSlotBudget = 8192;
 
 #ifdef __CUDACC__
 #define LTJK_HD __host__ __device__
@@ -70,8 +81,11 @@ static_assert(sizeof(AccInstr) == 8, "AccInstr layout");
 struct TileProg {
   int hrr_level0, nhrr_level;  // level ranges in ProgramSet::levels
   int out_base;                // HRR slot of output 0 (outputs contiguous)
-  int nout;                    // outputs of the tile (na nb nc nd)
+  int nout;                    // outputs of the tile (na nb nc nd, na = this tile's a range)
   int hrr_size;                // HRR slots beyond the accumulators this tile uses
+  int a0, na;                  // a's Cartesian components [a0, a0 + na) (derivatives: all)
+  int store_off;               // offset of the tile's first output in the stored blocks:
+                               // value a0 nb nc nd; derivative tile * (na nb nc nd)
 };
 
 // Device view of one class program (offsets into the shared instruction pools).
@@ -82,12 +96,12 @@ struct ClassProg {
   int vrr_begin, nvrr_level;  // level ranges are in level_pool[vrr_level0 .. +nvrr_level]
   int vrr_level0;
   int acc_begin, nacc;
-  int ntile, tile_begin;     // output tiles (1 plain; 9 = centre A,B,C x xyz for deriv)
+  int ntile, tile_begin;     // output tiles (plain: ranges of a; 9 = centre A,B,C x xyz for deriv)
   int vrr_size;   // slots of one VRR region (slot 0 = zero, 1..ltot+1 = base values)
   int acc_size;   // slots of one accumulator channel
   int hrr_size;   // HRR slots beyond the accumulators, max over tiles (slot acc_total = zero)
   int acc_total;  // nchan * acc_size
-  int nout;       // outputs per tile (na nb nc nd)
+  int nout;       // outputs of the whole block (na nb nc nd); derivatives: per tile
   int nh;         // 1 + largest integer multiplier of a VRR step
   double vrr_flops, hrr_flops;  // flop model: per primitive quartet / per contracted quartet
 };

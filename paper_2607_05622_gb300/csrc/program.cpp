@@ -326,19 +326,28 @@ void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv
   P.nacc = (int)accs.size();
   ps.acc.insert(ps.acc.end(), accs.begin(), accs.end());
 
-  // HRR to the outputs, in tiles.  Plain integrals: one tile with every output.
-  // Derivatives: nine tiles, one per (centre, direction), each
-  //   out[abcd] = chan_centre(raised) - n_x * chan0(lowered);
-  // every tile reuses the same work region, so the region only has to hold the
-  // largest tile (the output tiling of the paper's codegen discussion).
+  // HRR to the outputs, in tiles.  Derivatives: nine tiles, one per (centre,
+  // direction), each out[abcd] = chan_centre(raised) - n_x * chan0(lowered).
+  // Plain integrals: tiles over ranges of a's Cartesian components, each the
+  // row-major sub-block [a0, a0 + na) x [nb][nc][nd] of the output block; one
+  // tile when the whole block's recurrence fits the slot budget, else the
+  // fewest equal ranges that do (the output tiling of the paper's codegen
+  // discussion; a tile recomputes the intermediates it shares with others).
+  // Every tile reuses the same work region, so the region only has to hold
+  // the largest tile.
   auto ma = monos(la), mb = monos(lb), mc = monos(lc), md = monos(ld);
-  const int ntile = deriv ? 9 : 1;
-  P.ntile = ntile;
-  P.tile_begin = (int)ps.tiles.size();
   P.nout = ncart(la) * ncart(lb) * ncart(lc) * ncart(ld);
-  P.hrr_size = 0;
-  P.hrr_flops = 0;
-  for (int tile = 0; tile < ntile; ++tile) {
+  const int blk = P.nout / ncart(la);  // outputs per a component
+  struct Tile {
+    TileProg T{};
+    std::vector<HrrInstr> instr;   // level-ordered, slots final
+    std::vector<int> bounds;       // level boundaries (indices into instr)
+    double flops = 0;
+  };
+  // one tile: outputs with a in [a_lo, a_hi) (all for derivatives), for
+  // derivative tile `dtile` (centre dtile / 3, direction dtile % 3) or -1
+  auto make_tile = [&](int dtile, int a_lo, int a_hi) {
+    Tile out;
     HrrGen hg;
     hg.E = &E;
     hg.F = &F;
@@ -348,14 +357,15 @@ void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv
     const int zero = P.acc_total;
     std::vector<HrrInstr> final_instr;
     std::vector<int> final_level;
-    const int centre = tile / 3, x = tile % 3;
-    for (auto &a : ma)
+    const int centre = dtile / 3, x = dtile % 3;
+    for (int ia = a_lo; ia < a_hi; ++ia) {
+      const Mono &a = ma[ia];
       for (auto &b : mb)
         for (auto &c : mc)
           for (auto &d : md) {
             HrrInstr in{};
             in.kind = 2;  // t = s0 - n * s1
-            if (!deriv) {
+            if (dtile < 0) {
               int s = hg.get(0, a, b, c, d);
               in.s0 = (uint16_t)s;
               in.s1 = (uint16_t)zero;
@@ -381,8 +391,12 @@ void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv
             }
             final_instr.push_back(in);
           }
-    TileProg T{};
+    }
+    TileProg &T = out.T;
     T.nout = (int)final_instr.size();
+    T.a0 = a_lo;
+    T.na = a_hi - a_lo;
+    T.store_off = dtile < 0 ? a_lo * blk : dtile * P.nout;
     const int nodes_end = hg.acc_total + (int)hg.level.size();  // first output node
     if (nodes_end + T.nout > 65000) throw std::runtime_error("HRR output block too large");
     for (size_t k = 0; k < final_instr.size(); ++k) {
@@ -411,30 +425,77 @@ void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv
     const std::vector<int> pool_map =
         assign_slots(nodes_end, fixed, lev, tgt, src, std::vector<char>(nodes_end, 0), &pool_size);
     const int pool_base = T.out_base + T.nout;
-    auto remap = [&](int x) {
-      if (x < fixed) return x;
-      if (x >= nodes_end) return T.out_base + (x - nodes_end);
-      return pool_base + (pool_map[x] - fixed);
+    auto remap = [&](int v) {
+      if (v < fixed) return v;
+      if (v >= nodes_end) return T.out_base + (v - nodes_end);
+      return pool_base + (pool_map[v] - fixed);
     };
-    T.hrr_level0 = (int)ps.levels.size();
     int cur = -1;
     for (int k : order) {
       if (hg.instr_level[k] != cur) {
         cur = hg.instr_level[k];
-        ps.levels.push_back((int)ps.hrr.size());
+        out.bounds.push_back((int)out.instr.size());
       }
       HrrInstr in = hg.instr[k];
       in.tgt = (uint16_t)remap(in.tgt);
       in.s0 = (uint16_t)remap(in.s0);
       in.s1 = (uint16_t)remap(in.s1);
-      ps.hrr.push_back(in);
+      out.instr.push_back(in);
     }
-    ps.levels.push_back((int)ps.hrr.size());
-    T.nhrr_level = (int)ps.levels.size() - 1 - T.hrr_level0;
+    out.bounds.push_back((int)out.instr.size());
+    T.nhrr_level = (int)out.bounds.size() - 1;
     T.hrr_size = 1 + T.nout + (pool_size - fixed);  // zero slot, outputs, pool
-    P.hrr_size = std::max(P.hrr_size, T.hrr_size);
-    P.hrr_flops += hg.flops;
-    ps.tiles.push_back(T);
+    if (P.acc_total + T.hrr_size > 65000) throw std::runtime_error("HRR tile too large");
+    out.flops = hg.flops;
+    return out;
+  };
+  std::vector<Tile> tiles;
+  if (deriv) {
+    for (int t = 0; t < 9; ++t) tiles.push_back(make_tile(t, 0, ncart(la)));
+  } else {
+    // fewest a-ranges whose tiles fit: the class's slots (accumulators and
+    // the larger of the vertical region and the tile's horizontal region)
+    // within kTileSlotBudget, or, where the accumulators and the vertical
+    // region alone exceed it, a horizontal region no larger than the
+    // vertical one; one component per tile is the last resort
+    const int na = ncart(la);
+    const int limit = std::max(kTileSlotBudget, P.acc_total + P.vrr_size);
+    for (int nt = 1; nt <= na; ++nt) {
+      const int chunk = (na + nt - 1) / nt;
+      if (nt > 1 && (na + chunk - 1) / chunk != nt) continue;  // same ranges as a smaller count
+      std::vector<Tile> cand;
+      bool fits = true;
+      try {
+        for (int a0 = 0; a0 < na; a0 += chunk) {
+          cand.push_back(make_tile(-1, a0, std::min(na, a0 + chunk)));
+          if (P.acc_total + std::max(P.vrr_size, cand.back().T.hrr_size) > limit) {
+            fits = false;
+            if (chunk > 1) break;  // try more tiles; one component per tile is the last resort
+          }
+        }
+      } catch (const std::runtime_error &) {
+        if (chunk == 1) throw;
+        fits = false;
+      }
+      if (fits || chunk == 1) {
+        tiles = std::move(cand);
+        break;
+      }
+    }
+  }
+  P.ntile = (int)tiles.size();
+  P.tile_begin = (int)ps.tiles.size();
+  P.hrr_size = 0;
+  P.hrr_flops = 0;
+  for (Tile &t : tiles) {
+    t.T.hrr_level0 = (int)ps.levels.size();
+    const int base = (int)ps.hrr.size();
+    for (size_t L = 0; L + 1 < t.bounds.size(); ++L) ps.levels.push_back(base + t.bounds[L]);
+    ps.levels.push_back(base + t.bounds.back());
+    ps.hrr.insert(ps.hrr.end(), t.instr.begin(), t.instr.end());
+    P.hrr_size = std::max(P.hrr_size, t.T.hrr_size);
+    P.hrr_flops += t.flops;
+    ps.tiles.push_back(t.T);
   }
 }
 
@@ -452,7 +513,7 @@ static void validate(const ProgramSet &ps, const ClassProg &P) {
       if (sl >= P.vrr_size) bad("VRR slot out of range");
     if (in.tgt <= P.ltot + 1) bad("VRR overwrites a base slot");
     if (in.kind > 1 || in.dir > 2) bad("VRR kind/dir");
-    if (in.n1 >= 2 * kMaxLDeriv + 2 || in.n2 >= 2 * kMaxLDeriv + 2) bad("VRR multiplier");
+    if (in.n1 >= kNhMax || in.n2 >= kNhMax || P.nh > kNhMax) bad("VRR multiplier");
   }
   // the steps of one level run concurrently on the lanes of a warp: none may
   // write a slot that the level reads, and no two may write the same slot
@@ -497,7 +558,20 @@ static void validate(const ProgramSet &ps, const ClassProg &P) {
       if (in.tgt <= P.acc_total) bad("HRR overwrites an accumulator or the zero slot");
       if (in.kind > 2 || (in.kind < 2 && in.dir > 2)) bad("HRR kind/dir");
     }
-    if (T.out_base + T.nout > hmax || T.nout != P.nout) bad("output block");
+    if (T.out_base + T.nout > hmax) bad("output block");
+    const int blk = P.nout / ncart(P.la);
+    if (T.na < 1 || T.a0 < 0 || T.a0 + T.na > ncart(P.la) || T.nout != T.na * blk) bad("tile range");
+    if (P.deriv ? (T.na != ncart(P.la) || T.store_off != t * P.nout) : T.store_off != T.a0 * blk)
+      bad("tile store offset");
+  }
+  if (!P.deriv) {  // value tiles cover the a components in order
+    int next = 0;
+    for (int t = 0; t < P.ntile; ++t) {
+      const TileProg &T = ps.tiles[P.tile_begin + t];
+      if (T.a0 != next) bad("value tiles out of order");
+      next += T.na;
+    }
+    if (next != ncart(P.la)) bad("value tiles do not cover the block");
   }
 }
 
@@ -505,12 +579,13 @@ void build_programs(ProgramSet &ps) {
   ps = ProgramSet{};
   ps.progs.resize(2 * kNumPairClass * kNumPairClass);
   for (int deriv = 0; deriv <= 1; ++deriv)
-    for (int la = 0; la <= kMaxL; ++la)
+    for (int la = 0; la <= (deriv ? kMaxLGrad : kMaxL); ++la)
       for (int lb = 0; lb <= la; ++lb)
-        for (int lc = 0; lc <= kMaxL; ++lc)
+        for (int lc = 0; lc <= (deriv ? kMaxLGrad : kMaxL); ++lc)
           for (int ld = 0; ld <= lc; ++ld)
             build_one_program(ps, la, lb, lc, ld, deriv, ps.progs[quartet_index(la, lb, lc, ld, deriv)]);
-  for (const ClassProg &P : ps.progs) validate(ps, P);
+  for (const ClassProg &P : ps.progs)
+    if (P.nout) validate(ps, P);  // derivative classes above kMaxLGrad stay empty
 }
 
 }  // namespace ltjk

@@ -429,6 +429,10 @@ int ltjk_service_submit(ltjk_service *s, const ltjk_request *r, uint64_t *ticket
     if (!r->D || (!r->J && !r->K)) return set_error(LTJK_EINVAL, "service_submit: J/K request needs D and J or K");
   } else if (r->kind == LTJK_REQ_GRAD) {
     if (!r->P || !r->Q || !r->grad) return set_error(LTJK_EINVAL, "service_submit: gradient request needs P, Q, grad");
+    for (int sh = 0; sh < r->ctx->nshells; ++sh)
+      if (r->ctx->sh_l[sh] > kMaxLGrad)
+        return set_error(LTJK_EUNSUPPORTED, "service_submit: gradient of a context with l = %d above "
+                         "LTJK_MAX_L_GRAD = %d", r->ctx->sh_l[sh], kMaxLGrad);
   } else {
     return set_error(LTJK_EINVAL, "service_submit: unknown request kind %d", r->kind);
   }

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libltjk.so")
 OK, EINVAL, ENOMEM, EBUDGET, EUNSUPPORTED, ECUDA, ETIMEDOUT, ECANCELLED, ENOTREADY = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
 FP64, MIXED, FP64_NATIVE = 0, 1, 2
-MAX_L = 2
+MAX_L = 3          # largest shell l of the J/K build (f)
+MAX_L_GRAD = 2     # largest shell l of the gradient adjoint (d)
 
 
 class LtjkError(RuntimeError):

@@ -17,6 +17,13 @@ Recipe (one ``numpy.random.default_rng(seed)`` per workload; draw order fixed):
 Basis sets: heavy atom 3s2p1d (15 Cartesian AO), central heavy atom 4s3p2d
 (25 AO), H 2s1p (5 AO).  Electron counts use Z = 6 for heavy atoms, 12 for the
 central atom and 1 for H; o = electrons / 2.
+
+f-shell (triple-zeta-shaped) workloads stand in for the paper's f-shell
+systems (def2-TZVP / cc-pVTZ-class bases): heavy atom 4s3p2d1f (35 Cartesian
+AO), H 3s2p1d (15 AO), drawn by ``draw_tz_bases`` with the same per-shell
+recipe (step 1) for the kinds heavy_tz then H_tz, in place of step 1, except
+that f exponents are log-uniform in [0.2, 5] (f shells are polarization
+functions: def2-TZVP-class f exponents lie near 0.5-2).
 """
 from __future__ import annotations
 
@@ -30,9 +37,14 @@ KIND_SHELLS = {
     "central": (0, 0, 0, 0, 1, 1, 1, 2, 2),
     "H": (0, 0, 1),
 }
-KIND_Z = {"heavy": 6, "central": 12, "H": 1}
+KIND_Z = {"heavy": 6, "central": 12, "H": 1, "heavy_tz": 6, "H_tz": 1}
+TZ_KIND_SHELLS = {
+    "heavy_tz": (0, 0, 0, 0, 1, 1, 1, 2, 2, 3),
+    "H_tz": (0, 0, 0, 1, 1, 2),
+}
 NPRIM = 3
 EXP_RANGE = (0.1, 5.0e3)
+EXP_RANGE_F = (0.2, 5.0)
 
 
 def ncart(l: int) -> int:
@@ -70,18 +82,29 @@ class Molecule:
         return dataclasses.replace(self, coords=np.ascontiguousarray(coords, dtype=np.float64))
 
 
-def draw_kind_bases(rng: np.random.Generator) -> dict:
+def draw_kind_bases(rng: np.random.Generator, kind_shells: dict | None = None) -> dict:
     """Per element kind: list of (l, exps[3], coefs[3])."""
     out = {}
-    lo, hi = math.log(EXP_RANGE[0]), math.log(EXP_RANGE[1])
-    for kind in ("heavy", "central", "H"):
+    kind_shells = KIND_SHELLS if kind_shells is None else kind_shells
+    for kind in kind_shells:
         shells = []
-        for l in KIND_SHELLS[kind]:
+        for l in kind_shells[kind]:
+            lo, hi = (math.log(v) for v in (EXP_RANGE_F if l == 3 else EXP_RANGE))
             e = np.sort(np.exp(rng.uniform(lo, hi, NPRIM)))[::-1].copy()
             c = 1.0 - rng.random(NPRIM)
             shells.append((l, e, c))
         out[kind] = shells
     return out
+
+
+def draw_tz_bases(rng: np.random.Generator) -> dict:
+    """The f-shell kinds: heavy_tz 4s3p2d1f, H_tz 3s2p1d."""
+    return draw_kind_bases(rng, TZ_KIND_SHELLS)
+
+
+def tz_kinds(kinds):
+    """The f-shell counterpart of every atom kind of a geometry."""
+    return [{"heavy": "heavy_tz", "central": "heavy_tz", "H": "H_tz"}[k] for k in kinds]
 
 
 def build_molecule(coords, kinds, bases) -> Molecule:
@@ -199,9 +222,11 @@ def _mo_part(rng, mol: Molecule, nocc: int, npair: int):
 
 
 def jk_workload(name: str, coords, kinds, seed: int, npair: int, nlap: int,
-                nocc: int | None = None, tau: float = 1e-12) -> JKWorkload:
+                nocc: int | None = None, tau: float = 1e-12, tz: bool = False) -> JKWorkload:
     rng = np.random.default_rng(seed)
-    bases = draw_kind_bases(rng)
+    bases = draw_tz_bases(rng) if tz else draw_kind_bases(rng)
+    if tz:
+        kinds = tz_kinds(kinds)
     mol = build_molecule(coords, kinds, bases)
     if nocc is None:
         nocc = mol.nelec // 2
@@ -238,6 +263,28 @@ def small_chain(n_heavy: int, n_h: int, seed: int, npair: int = 1, nlap: int = 4
     w = jk_workload(f"chain {n_heavy}+{n_h}", c, k, seed=rng_seed, npair=npair, nlap=nlap,
                     tau=tau)
     return w
+
+
+def water_tz(seed: int = 11, npair: int = 1, nlap: int = 4, tau: float = 0.0) -> JKWorkload:
+    """65-AO water-like molecule in the f-shell basis (O-like 4s3p2d1f, two H 3s2p1d)."""
+    c, k = water_like()
+    return jk_workload("water-like f-shell 65 AO", c, k, seed=seed, npair=npair, nlap=nlap, tau=tau,
+                       tz=True)
+
+
+def small_chain_tz(n_heavy: int, n_h: int, seed: int, npair: int = 1, nlap: int = 4,
+                   tau: float = 0.0) -> JKWorkload:
+    """Small f-shell chain for parity tests."""
+    c, k = chain(n_heavy, n_h)
+    return jk_workload(f"f-shell chain {n_heavy}+{n_h}", c, k, seed=2000 + seed, npair=npair, nlap=nlap,
+                       tau=tau, tz=True)
+
+
+def config_fshell() -> JKWorkload:
+    """200-AO f-shell chain: 4 heavy 4s3p2d1f + 4 H 3s2p1d, 3 pairs x 16 points."""
+    c, k = chain(4)
+    return jk_workload("f-shell chain 200 AO, 48 densities", c, k, seed=6, npair=3, nlap=16,
+                       tau=1e-12, tz=True)
 
 
 @dataclasses.dataclass

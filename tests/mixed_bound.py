@@ -21,9 +21,10 @@ import numpy as np
 # 3.6e-3 on the 40-AO chain.  The margin covers the kernel's own rounding
 # order (its stage-1 set-up in double-float, its primitive-group reduction).
 EPS32 = 1e-2
-# binary32 digestion: at most 36 products and partial sums per placement
-# element, plus the rounding of D: gamma_40 with u = 2^-24.
-EPS_DIG = 40 * 2.0 ** -24
+# binary32 digestion: at most 100 products and partial sums per placement
+# element (an f x f density block), plus the rounding of D: gamma_104 with
+# u = 2^-24.
+EPS_DIG = 104 * 2.0 ** -24
 
 
 def shell_block_abs(mol, D):

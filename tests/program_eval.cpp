@@ -30,25 +30,31 @@ const ProgramSet &programs() {
 
 // F_m(T), m = 0..mmax: the convergent series e^{-T} sum_k (2T)^k / ((2m+1)(2m+3)...(2m+2k+1))
 // evaluated for F_mmax and descended; for large T the erf form and upward recursion.
-void boys(int mmax, double T, double *F) {
-  if (T < 30.0) {
+template <typename R>
+void boys(int mmax, R Tr, R *F) {
+  const long double T = Tr;
+  if (T < 30.0L) {
     long double term = 1.0L / (2 * mmax + 1), sum = term;
     for (int k = 1; k < 400; ++k) {
       term *= 2.0L * T / (2 * mmax + 2 * k + 1);
       sum += term;
       if (term < 1e-22L * sum) break;
     }
-    const long double e = std::exp(-(long double)T);
+    const long double e = std::exp(-T);
     long double f = e * sum;
-    F[mmax] = (double)f;
+    F[mmax] = (R)f;
     for (int m = mmax - 1; m >= 0; --m) {
       f = (2.0L * T * f + e) / (2 * m + 1);
-      F[m] = (double)f;
+      F[m] = (R)f;
     }
   } else {
-    const double e = std::exp(-T);
-    F[0] = 0.5 * std::sqrt(M_PI / T) * std::erf(std::sqrt(T));
-    for (int m = 0; m < mmax; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) / (2.0 * T);
+    const long double e = std::exp(-T), pi = 3.141592653589793238462643383279503L;
+    long double f = 0.5L * std::sqrt(pi / T) * std::erf(std::sqrt(T));
+    F[0] = (R)f;
+    for (int m = 0; m < mmax; ++m) {
+      f = ((2 * m + 1) * f - e) / (2.0L * T);
+      F[m + 1] = (R)f;
+    }
   }
 }
 
@@ -68,11 +74,11 @@ namespace {
 // Base values [00|00]^(m) (base[m], m = 0..ltot), the CoefSlot coefficients
 // and the n/(2 zeta), n/(2 eta), n/(2 (zeta+eta)) tables of the primitive
 // quartet (a, b | c, d) with full contraction coefficients ca..cd.
-void setup_primitive(const ClassProg &p, const double *A, const double *B, const double *C, const double *D,
-                     double a, double b, double c, double d, double coef, double *base, double *cf,
-                     double *h) {
-  const double zeta = a + b, eta = c + d, rho = zeta * eta / (zeta + eta);
-  double P[3], Q[3], W[3], ab2 = 0, cd2 = 0, pq2 = 0;
+template <typename R>
+void setup_primitive(const ClassProg &p, const R *A, const R *B, const R *C, const R *D, R a, R b, R c,
+                     R d, R coef, R *base, R *cf, R *h) {
+  const R zeta = a + b, eta = c + d, rho = zeta * eta / (zeta + eta);
+  R P[3], Q[3], W[3], ab2 = 0, cd2 = 0, pq2 = 0;
   for (int x = 0; x < 3; ++x) {
     P[x] = (a * A[x] + b * B[x]) / zeta;
     Q[x] = (c * C[x] + d * D[x]) / eta;
@@ -81,9 +87,9 @@ void setup_primitive(const ClassProg &p, const double *A, const double *B, const
     cd2 += (C[x] - D[x]) * (C[x] - D[x]);
     pq2 += (P[x] - Q[x]) * (P[x] - Q[x]);
   }
-  std::vector<double> F(p.ltot + 1);
-  boys(p.ltot, rho * pq2, F.data());
-  const double pre = 2.0 * std::pow(M_PI, 2.5) / (zeta * eta * std::sqrt(zeta + eta)) *
+  std::vector<R> F(p.ltot + 1);
+  boys<R>(p.ltot, rho * pq2, F.data());
+  const R pre = 2.0 * std::pow((R)3.141592653589793238462643383279503L, (R)2.5) / (zeta * eta * std::sqrt(zeta + eta)) *
                      std::exp(-a * b / zeta * ab2 - c * d / eta * cd2) * coef;
   for (int m = 0; m <= p.ltot; ++m) base[m] = pre * F[m];
   for (int x = 0; x < 3; ++x) {
@@ -114,55 +120,78 @@ void setup_primitive(const ClassProg &p, const double *A, const double *B, const
 // Gaussian x^l e^{-a r^2}) concatenated in shell order.  out [n0][n1][n2][n3].
 // deriv = 0: the value block [n0][n1][n2][n3]; deriv = 1: the nine derivative
 // tiles d/dA_x .. d/dC_z, each [n0][n1][n2][n3], concatenated.
-extern "C" int pe_quartet_d(int la, int lb, int lc, int ld, int deriv, const double *ctr, const int *np,
-                            const double *exps, const double *coefs, double *out) {
+namespace {
+
+template <typename R>
+int quartet_t(int la, int lb, int lc, int ld, int deriv, const double *ctr_d, const int *np,
+              const double *exps_d, const double *coefs_d, double *out) {
   const ProgramSet &ps = programs();
   if (la < lb || lc < ld) return -1;
   const ClassProg &p = ps.progs[quartet_index(la, lb, lc, ld, deriv)];
-  const double *A = ctr, *B = ctr + 3, *C = ctr + 6, *D = ctr + 9;
+  int nprim = 0;
+  for (int s = 0; s < 4; ++s) nprim += np[s];
+  const std::vector<R> ctr(ctr_d, ctr_d + 12), exps(exps_d, exps_d + nprim), coefs(coefs_d, coefs_d + nprim);
+  const R *A = ctr.data(), *B = A + 3, *C = A + 6, *D = A + 9;
   int off[5] = {0};
   for (int s = 0; s < 4; ++s) off[s + 1] = off[s] + np[s];
-  std::vector<double> acc(p.acc_total + p.hrr_size + 1, 0.0), v(p.vrr_size), cf(kNumCoef), h(3 * p.nh);
+  std::vector<R> acc(p.acc_total + p.hrr_size + 1, 0.0), v(p.vrr_size), cf(kNumCoef), h(3 * p.nh);
   for (int i = off[0]; i < off[1]; ++i)
     for (int j = off[1]; j < off[2]; ++j)
       for (int k = off[2]; k < off[3]; ++k)
         for (int l = off[3]; l < off[4]; ++l) {
-          v[0] = 0.0;
+          v[0] = 0;
           setup_primitive(p, A, B, C, D, exps[i], exps[j], exps[k], exps[l],
                           coefs[i] * coefs[j] * coefs[k] * coefs[l], v.data() + 1, cf.data(), h.data());
           for (int L = 0; L < p.nvrr_level; ++L)
             for (int s = ps.levels[p.vrr_level0 + L]; s < ps.levels[p.vrr_level0 + L + 1]; ++s) {
               const VrrInstr &in = ps.vrr[s];
-              double t = cf[kPAx + 3 * in.kind + in.dir] * v[in.s0] + cf[kWPx + 3 * in.kind + in.dir] * v[in.s1];
+              R t = cf[kPAx + 3 * in.kind + in.dir] * v[in.s0] + cf[kWPx + 3 * in.kind + in.dir] * v[in.s1];
               if (in.n1) t += h[in.kind * p.nh + in.n1] * (v[in.s2] - cf[kRhoZeta + in.kind] * v[in.s3]);
               if (in.n2) t += h[2 * p.nh + in.n2] * v[in.s4];
               v[in.tgt] = t;
             }
           for (int s = p.acc_begin; s < p.acc_begin + p.nacc; ++s) {
             const AccInstr &in = ps.acc[s];
-            acc[in.acc] += (in.chan == 0 ? 1.0 : cf[kWA + in.chan - 1]) * v[in.slot];
+            acc[in.acc] += (in.chan == 0 ? (R)1 : cf[kWA + in.chan - 1]) * v[in.slot];
           }
         }
-  double X[2][3];
+  R X[2][3];
   for (int x = 0; x < 3; ++x) {
     X[0][x] = A[x] - B[x];
     X[1][x] = C[x] - D[x];
   }
-  const std::vector<double> acc0(acc.begin(), acc.begin() + p.acc_total);
+  const std::vector<R> acc0(acc.begin(), acc.begin() + p.acc_total);
   for (int tile = 0; tile < p.ntile; ++tile) {
     const TileProg &T = ps.tiles[p.tile_begin + tile];
     std::copy(acc0.begin(), acc0.end(), acc.begin());
-    acc[p.acc_total] = 0.0;
+    acc[p.acc_total] = 0;
     for (int L = 0; L < T.nhrr_level; ++L)
       for (int s = ps.levels[T.hrr_level0 + L]; s < ps.levels[T.hrr_level0 + L + 1]; ++s) {
         const HrrInstr &in = ps.hrr[s];
-        const double c = in.kind < 2 ? X[in.kind][in.dir] : -double(in.dir);
+        const R c = in.kind < 2 ? X[in.kind][in.dir] : -(R)in.dir;
         acc[in.tgt] = c * acc[in.s1] + acc[in.s0];
       }
-    for (int o = 0; o < T.nout; ++o) out[(size_t)tile * T.nout + o] = acc[T.out_base + o];
+    for (int o = 0; o < T.nout; ++o) out[(size_t)T.store_off + o] = (double)acc[T.out_base + o];
   }
   return 0;
 }
+
+}  // namespace
+
+extern "C" int pe_quartet_d(int la, int lb, int lc, int ld, int deriv, const double *ctr, const int *np,
+                            const double *exps, const double *coefs, double *out) {
+  return quartet_t<double>(la, lb, lc, ld, deriv, ctr, np, exps, coefs, out);
+}
+
+// The same programs with every step in long double (64-bit significand on
+// x86, 113 bits on Arm): the rounding of a class's recurrences falls ~2^-11
+// (or more) below binary64's, which separates a wrong program from a badly
+// conditioned quartet.
+extern "C" int pe_quartet_ld(int la, int lb, int lc, int ld, int deriv, const double *ctr, const int *np,
+                             const double *exps, const double *coefs, double *out) {
+  return quartet_t<long double>(la, lb, lc, ld, deriv, ctr, np, exps, coefs, out);
+}
+
 
 #ifdef LTJK_GEN_HEADER
 // The same quartet through the straight-line source the generator emits for
@@ -289,7 +318,7 @@ extern "C" int pe_quartet_f32(int la, int lb, int lc, int ld, int deriv, const d
         const float c = in.kind < 2 ? X[in.kind][in.dir] : -float(in.dir);
         acc[in.tgt] = std::fma(c, acc[in.s1], acc[in.s0]);
       }
-    for (int o = 0; o < T.nout; ++o) out[(size_t)tile * T.nout + o] = acc[T.out_base + o];
+    for (int o = 0; o < T.nout; ++o) out[(size_t)T.store_off + o] = acc[T.out_base + o];
   }
   return 0;
 }

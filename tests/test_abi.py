@@ -198,7 +198,7 @@ def _basis(L, l, nprim=1, atom=0, exps=1.0):
 
 def test_context_create_checks_the_basis_on_the_host(L):
     """A basis the library cannot take is refused before the first CUDA call:
-    l above LTJK_MAX_L (f shells) is LTJK_EUNSUPPORTED, a bad primitive count,
+    l above LTJK_MAX_L (g shells) is LTJK_EUNSUPPORTED, a bad primitive count,
     atom index, exponent, precision or threshold LTJK_EINVAL."""
     lib = L.lib()
     h = ctypes.c_void_p()

@@ -91,6 +91,37 @@ def test_binary32_quartets_within_eps_of_schwarz(pe, oracle):
     assert worst > 1e-6
 
 
+def test_binary32_f_quartets_within_eps_of_schwarz(pe, oracle):
+    """The same on the f-shell chain (heavy 4s3p2d1f, H 3s2p1d): 1500 quartets
+    with an f shell sampled from those mixed mode evaluates in binary32, every
+    f class among them, error at most EPS32 Q_ab Q_cd."""
+    mol = W.small_chain_tz(2, 2, seed=4, tau=1e-12).mol
+    cn = oracle.norm_coefs(mol)
+    Q = oracle.schwarz(mol)
+    l = np.asarray(mol.shell_l)
+    ns = len(l)
+    cand = []
+    for s in itertools.product(range(ns), repeat=4):
+        if l[s[0]] < l[s[1]] or l[s[2]] < l[s[3]] or max(l[s[0]], l[s[2]]) < 3:
+            continue
+        if 1e-12 <= Q[s[0], s[1]] * Q[s[2], s[3]] <= 1e-6:
+            cand.append(s)
+    rng = np.random.default_rng(3)
+    sel = rng.choice(len(cand), size=min(1500, len(cand)), replace=False)
+    worst, seen = 0.0, set()
+    for i in sel:
+        s = cand[i]
+        qq = Q[s[0], s[1]] * Q[s[2], s[3]]
+        ref = oracle.shell_quartet(mol, *s)
+        got = _quartet(pe.pe_quartet_f32, mol, cn, s)
+        worst = max(worst, np.abs(got - ref).max() / qq)
+        seen.add(tuple(int(l[x]) for x in s))
+    print(f"f quartets in binary32: worst error / (Q_ab Q_cd) = {worst:.2e}, {len(seen)} classes")
+    assert len(seen) >= 30, len(seen)
+    assert worst <= EPS32, worst
+    assert worst > 1e-6
+
+
 def test_mixed_gate_from_the_bound(oracle):
     """The bound on the mixed GPU test's densities: small against max|J|, |K|,
     and zero when nothing is binary32 (promotion threshold below screening)."""

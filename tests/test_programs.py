@@ -7,7 +7,8 @@ import pytest
 
 from paper_2607_05622_gb300 import ltjk
 
-MAXL = 2
+MAXL = 3       # value classes: s, p, d, f
+MAXL_GRAD = 2  # derivative classes: s, p, d
 
 
 def ncart(l):
@@ -18,10 +19,10 @@ def span(lo, hi):
     return sum(ncart(l) for l in range(max(lo, 0), hi + 1))
 
 
-def classes():
-    for la in range(MAXL + 1):
+def classes(lmax=MAXL):
+    for la in range(lmax + 1):
         for lb in range(la + 1):
-            for lc in range(MAXL + 1):
+            for lc in range(lmax + 1):
                 for ld in range(lc + 1):
                     yield la, lb, lc, ld
 
@@ -39,7 +40,13 @@ def test_value_program_structure(L, q):
     la, lb, lc, ld = q
     p = L.class_program(la, lb, lc, ld, 0)
     assert p["ltot"] == la + lb + lc + ld
-    assert p["tiles"] == 1 and p["outputs"] == ncart(la) * ncart(lb) * ncart(lc) * ncart(ld)
+    # output tiles over ranges of a's components: the largest holds
+    # ceil(na / tiles) of them; the light classes keep the whole block in one
+    na, blk = ncart(la), ncart(lb) * ncart(lc) * ncart(ld)
+    assert 1 <= p["tiles"] <= na
+    assert p["outputs"] == -(-na // p["tiles"]) * blk
+    if max(q) <= 2 and la + lb + lc + ld <= 7:
+        assert p["tiles"] == 1
     # accumulators: [e0|f0] for l_a <= |e| <= l_a + l_b and l_c <= |f| <= l_c + l_d
     assert p["accumulators"] == span(la, la + lb) * span(lc, lc + ld)
     # every VRR level raises the total angular momentum by one
@@ -55,7 +62,7 @@ def test_value_program_structure(L, q):
     assert max(p["smem_per_warp"]) <= 227 * 1024
 
 
-@pytest.mark.parametrize("q", list(classes()))
+@pytest.mark.parametrize("q", list(classes(MAXL_GRAD)))
 def test_derivative_program_structure(L, q):
     la, lb, lc, ld = q
     p = L.class_program(la, lb, lc, ld, 1)
@@ -76,3 +83,17 @@ def test_symmetric_lookup_and_errors(L):
     assert e.value.code == L.EUNSUPPORTED
     with pytest.raises(L.LtjkError):
         L.class_program(0, 0, 0, 0, 2)
+    # derivative programs stop at d: an f shell's would need g recurrences
+    with pytest.raises(L.LtjkError) as e:
+        L.class_program(MAXL_GRAD + 1, 0, 0, 0, 1)
+    assert e.value.code == L.EUNSUPPORTED
+
+
+def test_f_classes_are_tiled_to_fit(L):
+    # (ff|ff): 10000 integrals; untiled its horizontal region alone is 35101
+    # slots (274 KB at 8 bytes), beyond one CTA's shared memory
+    p = L.class_program(3, 3, 3, 3)
+    assert p["tiles"] > 1
+    assert p["hrr_slots"] <= p["vrr_slots"]
+    assert max(p["smem_per_warp"]) <= 227 * 1024
+    assert p["accumulators"] == span(3, 6) ** 2

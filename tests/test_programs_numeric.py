@@ -1,8 +1,11 @@
 """The library's recurrence programs evaluated on the CPU (tests/program_eval.cpp
 interprets them with its own Boys function and primitive set-up) against the
 oracle's McMurchie-Davidson contracted blocks, one shell quartet of every value
-class from (ss|ss) to (dd|dd), bra and ket classes in both orders, at 1e-11
-relative to the block's largest element; and the derivative programs' nine
+class from (ss|ss) to (dd|dd), bra and ket classes in both orders, and of every
+class with an f shell up to (ff|ff) (whose output tiles are assembled into the
+block), at 1e-11 relative to the block's largest element (f classes: 1e-12 with
+the programs run in long double, 1e-8 in binary64, whose rounding the f
+blocks' horizontal recurrence amplifies); and the derivative programs' nine
 tiles, every class, against central differences of the oracle's blocks: the generator's
 vertical and horizontal steps, its compacted slots, channel weights and
 component order are right before any kernel runs them."""
@@ -37,7 +40,7 @@ def pe():
     return lib
 
 
-def _quartet(pe, oracle, mol, cn, shells):
+def _quartet(pe, oracle, mol, cn, shells, long_double=False):
     ls = [int(mol.shell_l[s]) for s in shells]
     ctr = np.concatenate([mol.coords[mol.shell_atom[s]] for s in shells]).astype(np.float64)
     off = np.concatenate([[0], np.cumsum(mol.shell_nprim)])
@@ -47,8 +50,9 @@ def _quartet(pe, oracle, mol, cn, shells):
     n = [(l + 1) * (l + 2) // 2 for l in ls]
     out = np.zeros(int(np.prod(n)))
     P = ctypes.POINTER(ctypes.c_double)
-    rc = pe.pe_quartet(*ls, ctr.ctypes.data_as(P), np_.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                       ex.ctypes.data_as(P), co.ctypes.data_as(P), out.ctypes.data_as(P))
+    args = (ctr.ctypes.data_as(P), np_.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+            ex.ctypes.data_as(P), co.ctypes.data_as(P), out.ctypes.data_as(P))
+    rc = pe.pe_quartet_ld(*ls, 0, *args) if long_double else pe.pe_quartet(*ls, *args)
     assert rc == 0
     return out.reshape(n)
 
@@ -72,6 +76,40 @@ def test_every_value_class_against_the_oracle(pe, oracle):
             assert np.abs(got - ref).max() <= 1e-11 * scale, ((la, lb, lc, ld), np.abs(got - ref).max() / scale)
             checked += 1
     assert checked == 36
+
+
+def test_every_f_value_class_against_the_oracle(pe, oracle):
+    w = W.small_chain_tz(2, 2, seed=7)  # heavy 4s3p2d1f + H 3s2p1d, several centres
+    mol = w.mol
+    cn = oracle.norm_coefs(mol)
+    by_l = {}
+    for s, l in enumerate(mol.shell_l):
+        by_l.setdefault(int(l), []).append(s)
+    rng = np.random.default_rng(2)
+    pairs = [(la, lb) for la in range(4) for lb in range(la + 1)]
+    checked = 0
+    for (la, lb) in pairs:
+        for (lc, ld) in pairs:
+            if max(la, lc) < 3:
+                continue
+            while True:  # at least two centres (one-centre blocks of odd total l vanish)
+                shells = [int(rng.choice(by_l[l])) for l in (la, lb, lc, ld)]
+                if len({int(mol.shell_atom[s]) for s in shells}) > 1:
+                    break
+            ref = oracle.shell_quartet(mol, *shells)
+            scale = np.abs(ref).max()
+            # the programs in long double pin their steps: 1e-12 of the block
+            got = _quartet(pe, oracle, mol, cn, shells, long_double=True)
+            err = np.abs(got - ref).max() / scale
+            assert err <= 1e-12, ((la, lb, lc, ld), err)
+            # in binary64 the horizontal transfer of these blocks amplifies
+            # rounding (up to ~5e-10 of the block measured on f quartets with
+            # d partners of exponent ~1e3): bounded, not a wrong step
+            got = _quartet(pe, oracle, mol, cn, shells)
+            err = np.abs(got - ref).max() / scale
+            assert err <= 1e-8, ((la, lb, lc, ld), err)
+            checked += 1
+    assert checked == 100 - 36
 
 
 def test_derivative_tiles_against_finite_differences(pe, oracle):
