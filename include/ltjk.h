@@ -107,10 +107,13 @@ typedef struct {
                   operation) on the FP32 pipe, which on GB300 is 58x faster
                   than its FP64 pipe; LTJK_FP64_NATIVE keeps every step in IEEE
                   binary64.  Both meet the FP64 parity gate (1e-10 relative to
-                  the oracle).  LTJK_MIXED evaluates the quartets above
-                  mixed_tau as LTJK_FP64 and the rest with binary32
-                  recurrences and digestion (their Boys function and set-up in
-                  double-float, rounded to binary32).  The accumulation across
+                  the oracle).  In LTJK_FP64 (and the promoted quartets of
+                  LTJK_MIXED) the classes with an f shell run in IEEE binary64:
+                  their recurrences amplify rounding ~1e4-fold, too much for
+                  double-float's ~2^-44 at that gate.  LTJK_MIXED evaluates
+                  the quartets above mixed_tau as LTJK_FP64 and the rest with
+                  binary32 recurrences and digestion (their Boys function and
+                  set-up in double-float, rounded to binary32).  The accumulation across
                   quartets is IEEE binary64 in every mode.
                   Range: each density is scaled by the exact power of two that
                   brings its largest element into [1/2, 1) before the
@@ -242,7 +245,9 @@ int ltjk_jk_build(ltjk_ctx *ctx, int ndens, const double *D, double *J, double *
    that cannot absorb the device-wide synchronisation of cudaMalloc/cudaFree.
    The paper has no counterpart; this is an interface convenience.
      Limit: 4 * ndens * N * N + ndens doubles (FP64 contexts) or
-     5 * ndens * N * N + ndens (mixed contexts) must not exceed 8 * 2^20;
+     5 * ndens * N * N + ndens (mixed contexts), two more ndens * N * N for
+     an FP64-class or mixed context with an f shell (binary64 density copies
+     beside the double-float ones), must not exceed 8 * 2^20;
      larger requests return LTJK_EINVAL with the sizes in ltjk_last_error().
      The first call on each device looks up the array's device address
      (cudaGetSymbolAddress) with that device current; make that first call
@@ -381,8 +386,8 @@ int ltjk_pseudo_density_factors(ltjk_ctx *ctx, int nocc, int nvir, const double 
 /* Contracted Cartesian integral blocks of nq shell quartets (a,b|c,d) given in
    shells_host[4*nq]; out [sum of block sizes] device FP64, blocks concatenated
    in order, each [na][nb][nc][nd] row-major.  Evaluated by the same kernels as
-   the build: double-float (LTJK_FP64), FP32 (LTJK_MIXED) or IEEE FP64
-   (LTJK_FP64_NATIVE). */
+   the build: double-float (LTJK_FP64; IEEE FP64 for classes with an f
+   shell), FP32 (LTJK_MIXED) or IEEE FP64 (LTJK_FP64_NATIVE). */
 int ltjk_shell_quartets(ltjk_ctx *ctx, int nq, const int *shells_host, int precision,
                         double *out, ltjk_stream stream);
 

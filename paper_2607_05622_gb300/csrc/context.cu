@@ -351,6 +351,10 @@ struct ltjk_ctx {
   int device = 0;
   ltjk_opts opts{};
   int natoms = 0, nshells = 0, nao = 0, npairs = 0;
+  // binary64 copies of the densities beside the double-float ones: a context
+  // with an f shell in an FP64-class or mixed mode runs those classes in
+  // IEEE binary64 (ieee64_class), whose digestion reads binary64 densities
+  bool ieee_copies = false;
   std::vector<double> coords;
   std::vector<int> sh_l, sh_atom, sh_ao, sh_nprim, sh_p0;
   std::vector<double> exps, ncoef;
@@ -510,7 +514,7 @@ int store_blocks(ltjk_ctx &c, const std::vector<std::pair<int, int>> &qs, int pr
     JKArgs a{};
     a.out = d_out;
     a.out_off = d_off.as<long long>();
-    if (prec == LTJK_FP64_NATIVE) {
+    if (prec == LTJK_FP64_NATIVE || (prec == LTJK_FP64 && ieee64_class(p.la, p.lb, p.lc, p.ld))) {
       ClassLaunch cl = make_launch(p, sizeof(double));
       rc = launch_class<double, kStore>(c.progs, cl,
                                         single_job(B, a, d_items.as<WorkItem>(), (int)items.size()), st);
@@ -654,7 +658,7 @@ int build_work(ltjk_ctx &c) {
 size_t jk_scratch_bytes(const ltjk_ctx *c, int nd) {
   const size_t n = (size_t)c->nao * c->nao * nd;
   return 4 * n * sizeof(double) + (c->opts.precision == LTJK_MIXED ? 2 * n * sizeof(float) : 0) +
-         (size_t)nd * sizeof(double);
+         (c->ieee_copies ? 2 * n * sizeof(double) : 0) + (size_t)nd * sizeof(double);
 }
 
 // Enqueue the per-density scales, the layout transposes and the accumulator
@@ -672,7 +676,9 @@ int jk_prologue(const ltjk_ctx *c, const double *D, void *base, int nd, bool wan
   const bool mixed = c->opts.precision == LTJK_MIXED;
   float *D32 = mixed ? reinterpret_cast<float *>(Kq + n) : nullptr;
   float *S32 = mixed ? D32 + n : nullptr;
-  double *scale = Kq + n + (mixed ? n : 0);
+  double *D64 = c->ieee_copies ? Kq + n + (mixed ? n : 0) : nullptr;  // beside the double-float copies
+  double *S64 = c->ieee_copies ? D64 + n : nullptr;
+  double *scale = Kq + n + (mixed ? n : 0) + (c->ieee_copies ? 2 * n : 0);
   JKArgs a{};
   if (native) {
     a.D = A;
@@ -680,6 +686,8 @@ int jk_prologue(const ltjk_ctx *c, const double *D, void *base, int nd, bool wan
   } else {
     a.D2 = reinterpret_cast<dflt *>(A);
     a.S2 = reinterpret_cast<dflt *>(Bq);
+    a.D = D64;
+    a.S = S64;
   }
   a.D32 = D32;
   a.S32 = S32;
@@ -689,7 +697,7 @@ int jk_prologue(const ltjk_ctx *c, const double *D, void *base, int nd, bool wan
   a.scale = scale;
   density_scales<<<nd, 256, 0, st>>>(D, (size_t)c->nao * c->nao, scale);
   const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16);
-  to_qinner<<<blocks, 256, 0, st>>>(D, native ? A : nullptr, native ? Bq : nullptr, D32, S32, nd,
+  to_qinner<<<blocks, 256, 0, st>>>(D, native ? A : D64, native ? Bq : S64, D32, S32, nd,
                                     c->nao, native ? nullptr : reinterpret_cast<dflt *>(A),
                                     native ? nullptr : reinterpret_cast<dflt *>(Bq), scale);
   CUDA_TRY(cudaGetLastError());
@@ -731,11 +739,12 @@ int launch_classes(ltjk_ctx *ctx, const JKArgs &a, cudaStream_t st) {
     if (w->n64) {
       cudaStream_t s2 = ctx->side[next++ % kSideStreams];
       const JobTable T = single_job(B, a, w->items64.as<WorkItem>(), w->n64);
+      const bool ieee = native || ieee64_class(p.la, p.lb, p.lc, p.ld);
       if (MODE == kJK)
-        rc = native ? launch_jk<double>(p, ctx->progs, T, s2) : launch_jk<dflt>(p, ctx->progs, T, s2);
+        rc = ieee ? launch_jk<double>(p, ctx->progs, T, s2) : launch_jk<dflt>(p, ctx->progs, T, s2);
       else
-        rc = native ? launch_class<double, MODE>(ctx->progs, make_launch(p, sizeof(double)), T, s2)
-                    : launch_class<dflt, MODE>(ctx->progs, make_launch(p, sizeof(dflt)), T, s2);
+        rc = ieee ? launch_class<double, MODE>(ctx->progs, make_launch(p, sizeof(double)), T, s2)
+                  : launch_class<dflt, MODE>(ctx->progs, make_launch(p, sizeof(dflt)), T, s2);
       if (rc) return rc;
     }
     if (w->n32) {
@@ -802,6 +811,7 @@ int ltjk_context_create(const ltjk_basis *bs, const ltjk_opts *opts, ltjk_ctx **
     c->sh_ao.push_back(c->nao);
     c->nao += ncart(l);
     np += n;
+    if (ieee64_class(l, 0, 0, 0) && c->opts.precision != LTJK_FP64_NATIVE) c->ieee_copies = true;
   }
   c->exps.assign(bs->exps_host, bs->exps_host + np);
   for (double e : c->exps)
@@ -1350,7 +1360,7 @@ extern "C" int ltjk_jk_build_noalloc(ltjk_ctx *ctx, int ndens, const double *D, 
   if (ndens < 1 || ndens > 4096)
     return set_error(LTJK_EINVAL, "jk_build_noalloc: ndens %d not in 1..4096", ndens);
   if (!J && !K) return LTJK_OK;
-  const size_t need = jk_scratch_bytes(ctx, ndens) / sizeof(double);  // 4 (or 5) n + ndens doubles
+  const size_t need = jk_scratch_bytes(ctx, ndens) / sizeof(double);  // 4 to 7 n + ndens doubles
   if (need > kNoallocDoubles)
     return set_error(LTJK_EINVAL,
                      "jk_build_noalloc: %d densities of %d AOs need %zu bytes of scratch, above the "

@@ -136,6 +136,17 @@ LTJK_HD constexpr bool gen_class(int la, int lb, int lc, int ld) {
          (la + lb + lc + ld <= 3 || (la + lb + lc + ld == 4 && ncart(la) * ncart(lb) * ncart(lc) * ncart(ld) <= 54));
 }
 
+// Classes whose FP64-class quartets run in IEEE binary64 instead of
+// double-float: those with an f shell.  Their vertical and horizontal
+// recurrences amplify rounding about 1e4-fold relative to Q_ab Q_cd (f
+// shells next to d shells of exponent ~1e3), which at double-float's
+// ~2^-44 per operation reached 1.7e-10 of max|K| on a 200-AO f-shell chain,
+// above the FP64 gate; binary64 leaves 4e-13.  s/p/d classes amplify less and
+// stay double-float.
+LTJK_HD constexpr bool ieee64_class(int la, int lb, int lc, int ld) {
+  return la >= 3 || lb >= 3 || lc >= 3 || ld >= 3;
+}
+
 void build_programs(ProgramSet &ps);
 void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv, ClassProg &out);
 // Straight-line C++/CUDA source of one class program (codegen.cpp).

@@ -101,10 +101,9 @@ struct ltjk_service {
 
 namespace {
 
-size_t job_bytes(const ltjk_request &r, int nao, bool mixed) {
-  const size_t n = (size_t)nao * nao * r.n;
-  if (r.kind == LTJK_REQ_JK)  // = jk_scratch_bytes
-    return 4 * n * sizeof(double) + (mixed ? 2 * n * sizeof(float) : 0) + (size_t)r.n * sizeof(double);
+size_t job_bytes(const ltjk_request &r) {
+  const size_t n = (size_t)r.ctx->nao * r.ctx->nao * r.n;
+  if (r.kind == LTJK_REQ_JK) return jk_scratch_bytes(r.ctx, r.n);
   return 2 * n * sizeof(double);
 }
 
@@ -144,7 +143,7 @@ int ltjk_service::step(std::vector<SvcJob *> &run, const StreamSet &S, int cap) 
           // the previous one to drain
           cudaStream_t st = S.side[q % kSideStreams];
           if (mode == 0) {
-            if (prec == 0)
+            if (prec == 0 && !ieee64_class(prog->la, prog->lb, prog->lc, prog->ld))
               launch_jk<dflt>(*prog, PR, T, st);
             else if (prec == 1)
               launch_jk<float>(*prog, PR, T, st);
@@ -438,7 +437,7 @@ int ltjk_service_submit(ltjk_service *s, const ltjk_request *r, uint64_t *ticket
   }
   auto j = std::make_unique<SvcJob>();
   j->req = *r;
-  j->bytes = job_bytes(*r, r->ctx->nao, r->ctx->opts.precision == LTJK_MIXED);
+  j->bytes = job_bytes(*r);
   if (!s->arena.could_fit(j->bytes))
     return set_error(LTJK_EBUDGET, "request needs %zu bytes (%zu rounded to the arena's %zu-byte blocks), "
                      "usable budget is %zu", j->bytes, Arena::rounded(j->bytes), Arena::kAlign, s->arena.size);

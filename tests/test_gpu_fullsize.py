@@ -1,5 +1,6 @@
 """Full-size parity in the launch configuration bench.py times: J/K of the
-200-AO chain (48 pseudo-densities, Schwarz 1e-12) and of the 445-AO macrocycle
+200-AO chain (48 pseudo-densities, Schwarz 1e-12), of the 200-AO f-shell
+chain (48 densities, FP64 class and mixed) and of the 445-AO macrocycle
 (128 densities, mixed precision) against oracle blocks computed one by one
 from the definition; the 200-AO gradient against central finite differences
 of the GPU FP64 energy and translational invariance."""
@@ -68,6 +69,37 @@ def test_chain200_fp64_and_mixed_sampled(L, oracle):
     JT, KT = c64.jk_build(D.transpose(1, 2).contiguous())
     assert float((KT - K.transpose(1, 2)).abs().max()) <= 1e-12 * sk
     assert float((JT - J).abs().max()) <= 1e-12 * sj
+
+
+def test_fshell_chain200_sampled(L, oracle):
+    w = W.config_fshell()
+    l = np.asarray(w.mol.shell_l)
+    fs = [s for s in range(len(l)) if l[s] == 3]
+    ds = [s for s in range(len(l)) if l[s] == 2]
+    pairs = [(fs[0], fs[0]), (fs[1], fs[-1]), (fs[2], ds[-1]), (ds[0], 0), (len(l) - 1, fs[1])]
+    c64 = L.Context(w.mol, schwarz_tau=w.schwarz_tau)
+    D = densities(L, c64, w)
+    J, K = c64.jk_build(D)
+    cmx = L.Context(w.mol, schwarz_tau=w.schwarz_tau, mixed_tau=1e-6, precision=L.MIXED)
+    Jm, Km = cmx.jk_build(D)
+    torch.cuda.synchronize()
+    sj, sk = float(J.abs().max()), float(K.abs().max())
+    off = oracle.shell_offsets(w.mol)
+    Dh = D.cpu().numpy()
+    e64, emx = [], []
+    for (a, b) in pairs:  # each oracle block once, against both builds
+        jb = oracle.j_block(w.mol, Dh, a, b, w.schwarz_tau)
+        kb = oracle.k_block(w.mol, Dh, a, b, w.schwarz_tau)
+        for (Jx, Kx, out) in ((J, K, e64), (Jm, Km, emx)):
+            Jg = Jx[:, off[a]:off[a + 1], off[b]:off[b + 1]].cpu().numpy()
+            Kg = Kx[:, off[a]:off[a + 1], off[b]:off[b + 1]].cpu().numpy()
+            out.append((np.abs(Jg - jb).max(), np.abs(Kg - kb).max()))
+    print("f-shell chain 200 AO: FP64 class %.2e, mixed %.2e of max |J|,|K|"
+          % (max(max(a / sj, b / sk) for a, b in e64), max(max(a / sj, b / sk) for a, b in emx)))
+    for ej, ek in e64:
+        assert ej <= 1e-10 * sj and ek <= 1e-10 * sk, (ej / sj, ek / sk)
+    for ej, ek in emx:
+        assert ej <= 1e-8 * sj and ek <= 1e-8 * sk, (ej / sj, ek / sk)
 
 
 def test_macrocycle445_mixed_sampled(L, oracle):
