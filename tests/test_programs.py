@@ -45,7 +45,7 @@ def test_value_program_structure(L, q):
     na, blk = ncart(la), ncart(lb) * ncart(lc) * ncart(ld)
     assert 1 <= p["tiles"] <= na
     assert p["outputs"] == -(-na // p["tiles"]) * blk
-    if max(q) <= 2 and la + lb + lc + ld <= 7:
+    if la + lb + lc + ld <= 6:
         assert p["tiles"] == 1
     # accumulators: [e0|f0] for l_a <= |e| <= l_a + l_b and l_c <= |f| <= l_c + l_d
     assert p["accumulators"] == span(la, la + lb) * span(lc, lc + ld)
