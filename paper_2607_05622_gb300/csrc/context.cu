@@ -1167,18 +1167,20 @@ int ltjk_jk_grad(ltjk_ctx *ctx, int nterms, const double *P, const double *Q, do
   CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t NN = (size_t)ctx->nao * ctx->nao, n = NN * nterms;
-  int rc = ctx->ensure_scratch(2 * n * sizeof(double), st);
+  int rc = ctx->ensure_scratch(4 * n * sizeof(double), st);
   if (rc) return rc;
   double *Pq = ctx->scratch.as<double>(), *Qq = Pq + n;
   const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16);
-  to_qinner<<<blocks, 256, 0, st>>>(P, Pq, nullptr, nullptr, nullptr, nterms, ctx->nao);
-  to_qinner<<<blocks, 256, 0, st>>>(Q, Qq, nullptr, nullptr, nullptr, nterms, ctx->nao);
+  to_qinner<<<blocks, 256, 0, st>>>(P, Pq, Qq + n, nullptr, nullptr, nterms, ctx->nao);
+  to_qinner<<<blocks, 256, 0, st>>>(Q, Qq, Qq + 2 * n, nullptr, nullptr, nterms, ctx->nao);
   CUDA_TRY(cudaGetLastError());
   g_launches += 2;
   CUDA_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 3 * ctx->natoms, st));
   JKArgs a{};
   a.P = Pq;
   a.Q = Qq;
+  a.S = Qq + n;      // P + P^T: the J images of Gamma read 4 words a term instead of 8
+  a.D = Qq + 2 * n;  // Q + Q^T
   a.nd = nterms;
   a.cJ = cJ;
   a.cK = cK;

@@ -617,7 +617,9 @@ __device__ void digest_jk(const JKArgs &a, const Real *I, const int off[4], cons
 
 // Gamma of one quartet for the gradient: the sum over the distinct images of
 // G_{mu nu ka rho} = sum_r [cJ P_r[mu][nu] Q_r[ka][rho] + cK P_r[mu][ka] Q_r[nu][rho]]
-// (Eq. jkderiv), times the degeneracy weight w, into gam[ijkl].
+// (Eq. jkderiv), times the degeneracy weight w, into gam[ijkl].  The J images
+// pair the symmetric sums, read from a.S = P + P^T and a.D = Q + Q^T (same
+// q-innermost layout as a.P, a.Q).
 __device__ void gamma_block(const JKArgs &a, double *gam, const int off[4], const int n[4],
                             double w, int N, int lane) {
   const int nq = n[0] * n[1] * n[2] * n[3];
@@ -642,8 +644,9 @@ __device__ void gamma_block(const JKArgs &a, double *gam, const int off[4], cons
 #define QX(x, y) __ldg(Q + ((x) * N + (y)) * nt)
         // a zero coefficient skips its images (warp-uniform branches)
         if (a.cJ != 0.0) {
-          const double gJ = (PX(mu, nu) + PX(nu, mu)) * (QX(ka, rho) + QX(rho, ka)) +
-                            (PX(ka, rho) + PX(rho, ka)) * (QX(mu, nu) + QX(nu, mu));
+          const double *Ps = a.S + r, *Qs = a.D + r;
+          const double gJ = __ldg(Ps + (mu * N + nu) * nt) * __ldg(Qs + (ka * N + rho) * nt) +
+                            __ldg(Ps + (ka * N + rho) * nt) * __ldg(Qs + (mu * N + nu) * nt);
           g = fma(a.cJ, gJ, g);
         }
         if (a.cK != 0.0) {

@@ -104,7 +104,7 @@ namespace {
 size_t job_bytes(const ltjk_request &r) {
   const size_t n = (size_t)r.ctx->nao * r.ctx->nao * r.n;
   if (r.kind == LTJK_REQ_JK) return jk_scratch_bytes(r.ctx, r.n);
-  return 2 * n * sizeof(double);
+  return 4 * n * sizeof(double);  // P, Q, P + P^T, Q + Q^T, q-innermost
 }
 
 // Bounded host wait on an event (polling); never blocks forever.
@@ -255,11 +255,11 @@ void ltjk_service::run() {
         j->scale = a.scale;
         g_launches -= 2;  // counted below with the others
       } else {
-        double *Pq = mem, *Qq = Pq + n;
-        to_qinner<<<blocks, 256, 0, st>>>(j->req.P, Pq, nullptr, nullptr, nullptr, j->req.n, c->nao);
-        to_qinner<<<blocks, 256, 0, st>>>(j->req.Q, Qq, nullptr, nullptr, nullptr, j->req.n, c->nao);
+        double *Pq = mem, *Qq = Pq + n, *Ps = Qq + n, *Qs = Ps + n;
+        to_qinner<<<blocks, 256, 0, st>>>(j->req.P, Pq, Ps, nullptr, nullptr, j->req.n, c->nao);
+        to_qinner<<<blocks, 256, 0, st>>>(j->req.Q, Qq, Qs, nullptr, nullptr, j->req.n, c->nao);
         cudaMemsetAsync(j->req.grad, 0, sizeof(double) * 3 * c->natoms, st);
-        a.P = Pq; a.Q = Qq; a.cJ = j->req.cJ; a.cK = j->req.cK; a.grad = j->req.grad;
+        a.P = Pq; a.Q = Qq; a.S = Ps; a.D = Qs; a.cJ = j->req.cJ; a.cK = j->req.cK; a.grad = j->req.grad;
       }
       a.nd = j->req.n;
       j->a = a;
