@@ -20,8 +20,9 @@
 //     place (AS > 1: one column of a lane-interleaved shared-memory block).
 //   template <typename Real, int AS = 1, int OS = 1> LTJK_GEN_FN void P_hrr(
 //       const Real *acc, const Real *X, Real *out);
-//     contracted accumulators acc[AS * i] -> output tiles out[OS * (tile *
-//     nout + o)]; X[0..2] = A - B, X[3..5] = C - D.
+//     contracted accumulators acc[AS * i] -> output tiles out[OS * (store_off
+//     + o)] (the tile's place in the block, or tile * nout for derivative
+//     tiles); X[0..2] = A - B, X[3..5] = C - D.
 // LTJK_GEN_FN is the function qualifier, defined by whoever includes the
 // emitted text (inline host+device code for the CPU checks, forced-inline
 // device code in the library).
@@ -174,7 +175,7 @@ std::string emit_class_source(const ProgramSet &ps, int la, int lb, int lc, int 
     }
     for (int q = 0; q < T.nout; ++q) {
       const Val v = hget(T.out_base + q);
-      o << "    out[OS * " << tile * T.nout + q << "] = " << (v.zero() ? "Real(0)" : v.expr) << ";\n";
+      o << "    out[OS * " << T.store_off + q << "] = " << (v.zero() ? "Real(0)" : v.expr) << ";\n";
     }
     o << "  }\n";
   }
