@@ -169,3 +169,38 @@ def test_service_refuses_f_shell_gradient(L):
         assert e.value.code == L.EUNSUPPORTED
     finally:
         svc.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_service_and_noalloc_with_f_shells(L, precision):
+    """J/K of an f-shell context through the service (f classes in binary64
+    beside double-float s/p/d classes in one step, alongside an s/p/d
+    context's request) and through the allocation-free entry point equal the
+    direct build."""
+    prec = L.FP64 if precision == "fp64" else L.MIXED
+    wf = W.water_tz()
+    ws = W.small_chain(2, 2, seed=4)
+    cf = L.Context(wf.mol, schwarz_tau=1e-12, mixed_tau=1e-6, precision=prec)
+    cs = L.Context(ws.mol, schwarz_tau=1e-12, mixed_tau=1e-6, precision=prec)
+    rng = np.random.default_rng(21)
+    Df = dev(rng.standard_normal((6, wf.mol.nao, wf.mol.nao)))
+    Ds = dev(rng.standard_normal((4, ws.mol.nao, ws.mol.nao)))
+    Jf0, Kf0 = cf.jk_build(Df)
+    Js0, Ks0 = cs.jk_build(Ds)
+    torch.cuda.synchronize()
+    svc = L.Service(1 << 30)
+    try:
+        t1, Jf, Kf = svc.submit_jk(cf, Df)
+        t2, Js, Ks = svc.submit_jk(cs, Ds)
+        svc.wait(t1, 120)
+        svc.wait(t2, 120)
+        for a, b in ((Jf, Jf0), (Kf, Kf0), (Js, Js0), (Ks, Ks0)):
+            assert relerr(a.cpu().numpy(), b.cpu().numpy()) <= 1e-12
+    finally:
+        svc.close()
+    J = torch.full_like(Df, np.nan)
+    K = torch.full_like(Df, np.nan)
+    cf.jk_build_noalloc(Df, J, K)
+    torch.cuda.synchronize()
+    assert relerr(J.cpu().numpy(), Jf0.cpu().numpy()) <= 1e-12
+    assert relerr(K.cpu().numpy(), Kf0.cpu().numpy()) <= 1e-12
