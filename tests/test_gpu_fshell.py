@@ -204,3 +204,30 @@ def test_service_and_noalloc_with_f_shells(L, precision):
     torch.cuda.synchronize()
     assert relerr(J.cpu().numpy(), Jf0.cpu().numpy()) <= 1e-12
     assert relerr(K.cpu().numpy(), Kf0.cpu().numpy()) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["dfloat", "mixed"])
+def test_f_only_molecules_max_primitives(L, oracle, prec):
+    """Degenerate f cases: one f shell of 8 primitives (the largest count; a
+    single (ff|ff) quartet, 4096 primitive quartets, on one centre) and two
+    atoms carrying one f shell each (only (ff|ff) quartets, three of them
+    unique), J and K of non-symmetric densities against the oracle."""
+    P = {"dfloat": L.FP64, "mixed": L.MIXED}[prec]
+    rng = np.random.default_rng(51)
+    e8 = np.sort(np.exp(rng.uniform(np.log(0.2), np.log(5.0), 8)))[::-1].copy()
+    c8 = 1.0 - rng.random(8)
+    e3 = np.array([2.1, 0.9, 0.35])
+    c3 = np.array([0.3, 0.6, 0.4])
+    one = W.build_molecule(np.zeros((1, 3)), ["X"], {"X": [(3, e8, c8)]})
+    two = W.build_molecule(np.array([[0.0, 0.0, 0.0], [0.3, -1.1, 2.4]]), ["X", "X"],
+                           {"X": [(3, e3, c3)]})
+    for mol in (one, two):
+        assert mol.nao == 10 * mol.natoms
+        ctx = L.Context(mol, schwarz_tau=0.0, mixed_tau=1e-6, precision=P)
+        D = rng.standard_normal((3, mol.nao, mol.nao))
+        J, K = ctx.jk_build(dev(D))
+        torch.cuda.synchronize()
+        Jr, Kr = oracle.jk(mol, D)
+        J, K = J.cpu().numpy(), K.cpu().numpy()
+        print(f"f only, {mol.natoms} atom(s), {prec}: J {relerr(J, Jr):.2e} K {relerr(K, Kr):.2e}")
+        assert relerr(J, Jr) <= TOL64 and relerr(K, Kr) <= TOL64
