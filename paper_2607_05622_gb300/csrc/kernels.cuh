@@ -247,9 +247,10 @@ __host__ __device__ inline int ptab_reals(const ClassProg &p, int T, size_t real
 }
 // Shared memory one warp needs for class program p with G groups and a T-entry
 // primitive table, in bytes: primitive table, G accumulator sets and the work
-// region (Real), then for the gradient the Gamma block of one quartet (double).
+// region (Real: 2G vertical regions, or the horizontal slots if larger), then
+// for the gradient the Gamma block of one quartet (double).
 __host__ __device__ inline size_t gamma_offset(const ClassProg &p, int G, int T, size_t real_bytes) {
-  int work = G * p.vrr_size > p.hrr_size ? G * p.vrr_size : p.hrr_size;
+  int work = 2 * G * p.vrr_size > p.hrr_size ? 2 * G * p.vrr_size : p.hrr_size;
   size_t b = (size_t)(ptab_reals(p, T, real_bytes) + G * p.acc_total + work) * real_bytes;
   return (b + 15) / 16 * 16;
 }
@@ -382,6 +383,7 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
   Real *work = acc0 + p.acc_total;              // VRR regions / HRR slots
   Real *my_acc = accs + (G - 1 - g) * p.acc_total;
   Real *my_vrr = work + g * p.vrr_size;
+  Real *my_vrr2 = work + (G + g) * p.vrr_size;  // the group's second primitive quartet
 
   const int2 sab = B.pair_sh[ip], scd = B.pair_sh[jp];
   const int pp0 = B.pair_pp0[ip], npp = B.pair_npp[ip];
@@ -398,43 +400,51 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
       stage1<Real>(B, p, ptab + lane * stride, ia, ic, sab, scd);
     }
     __syncwarp();
-    // stage 2: recurrences, G primitive quartets at a time
+    // stage 2: recurrences, 2G primitive quartets at a time: group g runs
+    // entries r0 + g and r0 + G + g, each lane applying every step it decodes
+    // to both (two independent chains per instruction load; 5 % faster than
+    // two steps of one primitive quartet per iteration)
     const int nchunk = min(T, npq - c0);
-    for (int r0 = 0; r0 < nchunk; r0 += G) {
-      const int loc = r0 + g;
-      const bool active = loc < nchunk;
+    for (int r0 = 0; r0 < nchunk; r0 += 2 * G) {
+      const int loc = r0 + g, loc2 = r0 + G + g;
+      const bool active = loc < nchunk, active2 = loc2 < nchunk;
       const Real *e = ptab + loc * stride;
       const Real *cf = e + p.ltot + 1;
       const Real *h = cf + kNumCoef;
+      const Real *e2 = ptab + (active2 ? loc2 : loc) * stride;
+      const Real *cf2 = e2 + p.ltot + 1;
+      const Real *h2 = cf2 + kNumCoef;
       if (active) {
         for (int t = s; t <= p.ltot + 1; t += S) my_vrr[t] = t == 0 ? zero_real<Real>() : e[t - 1];
+        for (int t = s; t <= p.ltot + 1; t += S) my_vrr2[t] = t == 0 ? zero_real<Real>() : e2[t - 1];
       }
       __syncwarp();
       for (int L = 0; L < p.nvrr_level; ++L) {
         const int i0 = PR.levels[p.vrr_level0 + L], i1 = PR.levels[p.vrr_level0 + L + 1];
         if (active) {
-          // two independent steps per lane per iteration: every source of both
-          // is read before either target is written (steps of one level never
-          // read each other), so the two dependency chains overlap; the
-          // optional operands are read only by the steps that use them (1 %
-          // faster than reading all five; four steps per iteration and
-          // eight-output digestion groups measured 1-3 % slower)
-          for (int k = i0 + s; k < i1; k += 2 * S) {
-            const bool two = k + S < i1;
+          // steps of one level never read each other's targets, so every
+          // source is read before any target of the level is written; the
+          // optional operands are read only by the steps that use them (four
+          // steps of one quartet per iteration and eight-output digestion
+          // groups measured 1-3 % slower)
+          for (int k = i0 + s; k < i1; k += S) {
             const VrrInstr ia = PR.vrr[k];
-            const VrrInstr ib = PR.vrr[two ? k + S : k];
-            const Real a0 = my_vrr[ia.s0], a1 = my_vrr[ia.s1];
-            const Real b0 = my_vrr[ib.s0], b1 = my_vrr[ib.s1];
-            Real ta = cf[kPAx + 3 * ia.kind + ia.dir] * a0;
-            Real tb = cf[kPAx + 3 * ib.kind + ib.dir] * b0;
-            ta = fma(cf[kWPx + 3 * ia.kind + ia.dir], a1, ta);
-            tb = fma(cf[kWPx + 3 * ib.kind + ib.dir], b1, tb);
-            if (ia.n1) ta = fma(h[ia.kind * nh + ia.n1], fma(-cf[kRhoZeta + ia.kind], my_vrr[ia.s3], my_vrr[ia.s2]), ta);
-            if (ib.n1) tb = fma(h[ib.kind * nh + ib.n1], fma(-cf[kRhoZeta + ib.kind], my_vrr[ib.s3], my_vrr[ib.s2]), tb);
-            if (ia.n2) ta = fma(h[2 * nh + ia.n2], my_vrr[ia.s4], ta);
-            if (ib.n2) tb = fma(h[2 * nh + ib.n2], my_vrr[ib.s4], tb);
+            const int c0 = kPAx + 3 * ia.kind + ia.dir;
+            Real ta = cf[c0] * my_vrr[ia.s0];
+            Real tb = cf2[c0] * my_vrr2[ia.s0];
+            ta = fma(cf[kWPx - kPAx + c0], my_vrr[ia.s1], ta);
+            tb = fma(cf2[kWPx - kPAx + c0], my_vrr2[ia.s1], tb);
+            if (ia.n1) {
+              const int hn = ia.kind * nh + ia.n1, rk = kRhoZeta + ia.kind;
+              ta = fma(h[hn], fma(-cf[rk], my_vrr[ia.s3], my_vrr[ia.s2]), ta);
+              tb = fma(h2[hn], fma(-cf2[rk], my_vrr2[ia.s3], my_vrr2[ia.s2]), tb);
+            }
+            if (ia.n2) {
+              ta = fma(h[2 * nh + ia.n2], my_vrr[ia.s4], ta);
+              tb = fma(h2[2 * nh + ia.n2], my_vrr2[ia.s4], tb);
+            }
             my_vrr[ia.tgt] = ta;
-            if (two) my_vrr[ib.tgt] = tb;
+            my_vrr2[ia.tgt] = tb;
           }
         }
         __syncwarp();
@@ -443,7 +453,12 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
         for (int k = p.acc_begin + s; k < p.acc_begin + p.nacc; k += S) {
           const AccInstr a = PR.acc[k];
           Real w = a.chan == 0 ? Real(1) : cf[kWA + a.chan - 1];
-          my_acc[a.acc] = fma(w, my_vrr[a.slot], my_acc[a.acc]);
+          Real v = fma(w, my_vrr[a.slot], my_acc[a.acc]);
+          if (active2) {
+            Real w2 = a.chan == 0 ? Real(1) : cf2[kWA + a.chan - 1];
+            v = fma(w2, my_vrr2[a.slot], v);
+          }
+          my_acc[a.acc] = v;
         }
       }
       __syncwarp();
