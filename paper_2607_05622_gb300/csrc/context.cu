@@ -198,14 +198,15 @@ int device_programs(int dev, DevProgs *out, const double **boys, const float2 **
 // Launch configuration of one class program: groups per warp from the average
 // width of a recurrence level, warps per CTA from the shared-memory budget.
 ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
-  // Candidate layouts: G groups of S lanes (two primitive quartets per group,
-  // its S lanes over the independent steps of each recurrence level, each
-  // step applied to both) and a T-entry primitive table (2G <= T; T shrinks
+  // Candidate layouts: G groups of S lanes, each group running P = 2 or 1
+  // primitive quartets (its S lanes over the independent steps of each
+  // recurrence level), and a T-entry primitive table (PG <= T; T shrinks
   // from 32 while the warp's shared memory would keep fewer than 16 warps on
   // an SM, as long as the digestion's offset table still fits in it).  Cost
   // per primitive quartet, in warp iterations: sum over levels of
-  // ceil(width / S) x S / 64 (one step per lane per iteration for two
-  // quartets, 2G = 64/S quartets share the warp), scaled by
+  // ceil(width / S) x S / 64 for P = 2 (one step per lane per iteration,
+  // applied to two quartets) or ceil(width / 2S) x S / 32 for P = 1 (two
+  // steps of one quartet per lane per iteration), scaled by
   // 16 / (warps per SM) when shared memory allows fewer than 16 warps (a
   // target of 12 measured 1 % slower, 8 measured 13 % slower).  The
   // cheapest layout wins; narrow levels favour small S, large programs
@@ -213,22 +214,24 @@ ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
   const ProgramSet &ps = g_prog.ps;
   ClassLaunch best{};
   double best_cost = 1e300;
+  for (int P = 2; P >= 1; --P)
   for (int S = 32; S >= 1; S /= 2) {
     ClassLaunch cl{};
     cl.p = p;
     cl.G = 32 / S;
+    cl.P = P;
     cl.T = 32;
-    cl.smem_per_warp = (int)warp_smem_bytes(p, cl.G, cl.T, real_bytes);
-    while (cl.T > 8 && cl.T / 2 >= 2 * cl.G && cl.smem_per_warp > kSmemPerSM / 16 &&
+    cl.smem_per_warp = (int)warp_smem_bytes(p, cl.G, cl.T, P, real_bytes);
+    while (cl.T > 8 && cl.T / 2 >= P * cl.G && cl.smem_per_warp > kSmemPerSM / 16 &&
            (size_t)(cl.T / 2) * pt_stride(p) * real_bytes >= digest_table_bytes(p)) {
       cl.T /= 2;
-      cl.smem_per_warp = (int)warp_smem_bytes(p, cl.G, cl.T, real_bytes);
+      cl.smem_per_warp = (int)warp_smem_bytes(p, cl.G, cl.T, P, real_bytes);
     }
     if (cl.smem_per_warp > kSmemBudget) continue;
     double cost = 0.0;
     for (int L = 0; L < p.nvrr_level; ++L) {
       const int w = ps.levels[p.vrr_level0 + L + 1] - ps.levels[p.vrr_level0 + L];
-      cost += (double)((w + S - 1) / S) * S / 64.0;
+      cost += P == 2 ? (double)((w + S - 1) / S) * S / 64.0 : (double)((w + 2 * S - 1) / (2 * S)) * S / 32.0;
     }
     cost += 1.0 / 32.0;  // per-quartet overheads: set-up share, syncs
     const int warps_sm = std::min(16, kSmemPerSM / (cl.smem_per_warp + kSmemPerCTAReserved));
@@ -242,7 +245,8 @@ ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
     best.p = p;
     best.G = 1;
     best.T = 8;
-    best.smem_per_warp = (int)warp_smem_bytes(p, 1, 8, real_bytes);
+    best.P = 1;
+    best.smem_per_warp = (int)warp_smem_bytes(p, 1, 8, 1, real_bytes);
   }
   best.warps = std::max(1, std::min(4, kSmemBudget / std::max(best.smem_per_warp, 1)));
   return best;

@@ -224,6 +224,7 @@ struct ClassLaunch {
   int warps;    // warps per CTA
   int smem_per_warp;  // bytes
   int T;        // primitive-table entries (set-up of T primitive quartets at a time)
+  int P;        // primitive quartets per group in the vertical recurrence (1 or 2)
 };
 
 // The digestion tabulates its output offsets in the dead primitive table: ten
@@ -247,15 +248,15 @@ __host__ __device__ inline int ptab_reals(const ClassProg &p, int T, size_t real
 }
 // Shared memory one warp needs for class program p with G groups and a T-entry
 // primitive table, in bytes: primitive table, G accumulator sets and the work
-// region (Real: 2G vertical regions, or the horizontal slots if larger), then
-// for the gradient the Gamma block of one quartet (double).
-__host__ __device__ inline size_t gamma_offset(const ClassProg &p, int G, int T, size_t real_bytes) {
-  int work = 2 * G * p.vrr_size > p.hrr_size ? 2 * G * p.vrr_size : p.hrr_size;
+// region (Real: P G vertical regions, or the horizontal slots if larger),
+// then for the gradient the Gamma block of one quartet (double).
+__host__ __device__ inline size_t gamma_offset(const ClassProg &p, int G, int T, int P, size_t real_bytes) {
+  int work = P * G * p.vrr_size > p.hrr_size ? P * G * p.vrr_size : p.hrr_size;
   size_t b = (size_t)(ptab_reals(p, T, real_bytes) + G * p.acc_total + work) * real_bytes;
   return (b + 15) / 16 * 16;
 }
-__host__ __device__ inline size_t warp_smem_bytes(const ClassProg &p, int G, int T, size_t real_bytes) {
-  size_t b = gamma_offset(p, G, T, real_bytes);
+__host__ __device__ inline size_t warp_smem_bytes(const ClassProg &p, int G, int T, int P, size_t real_bytes) {
+  size_t b = gamma_offset(p, G, T, P, real_bytes);
   if (p.deriv) b += (size_t)p.nout * sizeof(double);
   return (b + 15) / 16 * 16;
 }
@@ -374,7 +375,7 @@ __device__ __forceinline__ void stage1(const DevBasis &B, const ClassProg &p, Re
 // Reals, row-major [na][nb][nc][nd], or 9 such blocks for derivatives).
 template <typename Real>
 __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const ClassProg &p, int G, int T,
-                               Real *sm, int ip, int jp, int lane) {
+                               int P, Real *sm, int ip, int jp, int lane) {
   const int S = 32 / G, g = lane / S, s = lane % S;
   const int stride = pt_stride(p), nh = p.nh;
   Real *ptab = sm;                              // [T][stride] (and the digestion's table)
@@ -400,68 +401,118 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
       stage1<Real>(B, p, ptab + lane * stride, ia, ic, sab, scd);
     }
     __syncwarp();
-    // stage 2: recurrences, 2G primitive quartets at a time: group g runs
-    // entries r0 + g and r0 + G + g, each lane applying every step it decodes
-    // to both (two independent chains per instruction load; 5 % faster than
-    // two steps of one primitive quartet per iteration)
+    // stage 2: recurrences.  P = 2: 2G primitive quartets at a time, group
+    // g running entries r0 + g and r0 + G + g, each lane applying every
+    // step it decodes to both (two independent chains per instruction
+    // load; 5 % faster on the double-float and binary32 classes).  P = 1:
+    // G at a time, each lane taking two steps of one quartet per
+    // iteration (half the vertical regions: the binary64 f classes, bound
+    // by the FP64 pipe, keep their occupancy).
     const int nchunk = min(T, npq - c0);
-    for (int r0 = 0; r0 < nchunk; r0 += 2 * G) {
-      const int loc = r0 + g, loc2 = r0 + G + g;
-      const bool active = loc < nchunk, active2 = loc2 < nchunk;
-      const Real *e = ptab + loc * stride;
-      const Real *cf = e + p.ltot + 1;
-      const Real *h = cf + kNumCoef;
-      const Real *e2 = ptab + (active2 ? loc2 : loc) * stride;
-      const Real *cf2 = e2 + p.ltot + 1;
-      const Real *h2 = cf2 + kNumCoef;
-      if (active) {
-        for (int t = s; t <= p.ltot + 1; t += S) my_vrr[t] = t == 0 ? zero_real<Real>() : e[t - 1];
-        for (int t = s; t <= p.ltot + 1; t += S) my_vrr2[t] = t == 0 ? zero_real<Real>() : e2[t - 1];
-      }
-      __syncwarp();
-      for (int L = 0; L < p.nvrr_level; ++L) {
-        const int i0 = PR.levels[p.vrr_level0 + L], i1 = PR.levels[p.vrr_level0 + L + 1];
+    if (P == 2) {
+      for (int r0 = 0; r0 < nchunk; r0 += 2 * G) {
+        const int loc = r0 + g, loc2 = r0 + G + g;
+        const bool active = loc < nchunk, active2 = loc2 < nchunk;
+        const Real *e = ptab + loc * stride;
+        const Real *cf = e + p.ltot + 1;
+        const Real *h = cf + kNumCoef;
+        const Real *e2 = ptab + (active2 ? loc2 : loc) * stride;
+        const Real *cf2 = e2 + p.ltot + 1;
+        const Real *h2 = cf2 + kNumCoef;
         if (active) {
-          // steps of one level never read each other's targets, so every
-          // source is read before any target of the level is written; the
-          // optional operands are read only by the steps that use them (four
-          // steps of one quartet per iteration and eight-output digestion
-          // groups measured 1-3 % slower)
-          for (int k = i0 + s; k < i1; k += S) {
-            const VrrInstr ia = PR.vrr[k];
-            const int c0 = kPAx + 3 * ia.kind + ia.dir;
-            Real ta = cf[c0] * my_vrr[ia.s0];
-            Real tb = cf2[c0] * my_vrr2[ia.s0];
-            ta = fma(cf[kWPx - kPAx + c0], my_vrr[ia.s1], ta);
-            tb = fma(cf2[kWPx - kPAx + c0], my_vrr2[ia.s1], tb);
-            if (ia.n1) {
-              const int hn = ia.kind * nh + ia.n1, rk = kRhoZeta + ia.kind;
-              ta = fma(h[hn], fma(-cf[rk], my_vrr[ia.s3], my_vrr[ia.s2]), ta);
-              tb = fma(h2[hn], fma(-cf2[rk], my_vrr2[ia.s3], my_vrr2[ia.s2]), tb);
+          for (int t = s; t <= p.ltot + 1; t += S) my_vrr[t] = t == 0 ? zero_real<Real>() : e[t - 1];
+          for (int t = s; t <= p.ltot + 1; t += S) my_vrr2[t] = t == 0 ? zero_real<Real>() : e2[t - 1];
+        }
+        __syncwarp();
+        for (int L = 0; L < p.nvrr_level; ++L) {
+          const int i0 = PR.levels[p.vrr_level0 + L], i1 = PR.levels[p.vrr_level0 + L + 1];
+          if (active) {
+            // steps of one level never read each other's targets, so every
+            // source is read before any target of the level is written; the
+            // optional operands are read only by the steps that use them (four
+            // steps of one quartet per iteration and eight-output digestion
+            // groups measured 1-3 % slower)
+            for (int k = i0 + s; k < i1; k += S) {
+              const VrrInstr ia = PR.vrr[k];
+              const int c0 = kPAx + 3 * ia.kind + ia.dir;
+              Real ta = cf[c0] * my_vrr[ia.s0];
+              Real tb = cf2[c0] * my_vrr2[ia.s0];
+              ta = fma(cf[kWPx - kPAx + c0], my_vrr[ia.s1], ta);
+              tb = fma(cf2[kWPx - kPAx + c0], my_vrr2[ia.s1], tb);
+              if (ia.n1) {
+                const int hn = ia.kind * nh + ia.n1, rk = kRhoZeta + ia.kind;
+                ta = fma(h[hn], fma(-cf[rk], my_vrr[ia.s3], my_vrr[ia.s2]), ta);
+                tb = fma(h2[hn], fma(-cf2[rk], my_vrr2[ia.s3], my_vrr2[ia.s2]), tb);
+              }
+              if (ia.n2) {
+                ta = fma(h[2 * nh + ia.n2], my_vrr[ia.s4], ta);
+                tb = fma(h2[2 * nh + ia.n2], my_vrr2[ia.s4], tb);
+              }
+              my_vrr[ia.tgt] = ta;
+              my_vrr2[ia.tgt] = tb;
             }
-            if (ia.n2) {
-              ta = fma(h[2 * nh + ia.n2], my_vrr[ia.s4], ta);
-              tb = fma(h2[2 * nh + ia.n2], my_vrr2[ia.s4], tb);
+          }
+          __syncwarp();
+        }
+        if (active) {
+          for (int k = p.acc_begin + s; k < p.acc_begin + p.nacc; k += S) {
+            const AccInstr a = PR.acc[k];
+            Real w = a.chan == 0 ? Real(1) : cf[kWA + a.chan - 1];
+            Real v = fma(w, my_vrr[a.slot], my_acc[a.acc]);
+            if (active2) {
+              Real w2 = a.chan == 0 ? Real(1) : cf2[kWA + a.chan - 1];
+              v = fma(w2, my_vrr2[a.slot], v);
             }
-            my_vrr[ia.tgt] = ta;
-            my_vrr2[ia.tgt] = tb;
+            my_acc[a.acc] = v;
           }
         }
         __syncwarp();
       }
-      if (active) {
-        for (int k = p.acc_begin + s; k < p.acc_begin + p.nacc; k += S) {
-          const AccInstr a = PR.acc[k];
-          Real w = a.chan == 0 ? Real(1) : cf[kWA + a.chan - 1];
-          Real v = fma(w, my_vrr[a.slot], my_acc[a.acc]);
-          if (active2) {
-            Real w2 = a.chan == 0 ? Real(1) : cf2[kWA + a.chan - 1];
-            v = fma(w2, my_vrr2[a.slot], v);
-          }
-          my_acc[a.acc] = v;
+    } else {
+      for (int r0 = 0; r0 < nchunk; r0 += G) {
+        const int loc = r0 + g;
+        const bool active = loc < nchunk;
+        const Real *e = ptab + loc * stride;
+        const Real *cf = e + p.ltot + 1;
+        const Real *h = cf + kNumCoef;
+        if (active) {
+          for (int t = s; t <= p.ltot + 1; t += S) my_vrr[t] = t == 0 ? zero_real<Real>() : e[t - 1];
         }
+        __syncwarp();
+        for (int L = 0; L < p.nvrr_level; ++L) {
+          const int i0 = PR.levels[p.vrr_level0 + L], i1 = PR.levels[p.vrr_level0 + L + 1];
+          if (active) {
+            // two independent steps per lane per iteration (every source of
+            // both is read before either target is written)
+            for (int k = i0 + s; k < i1; k += 2 * S) {
+              const bool two = k + S < i1;
+              const VrrInstr ia = PR.vrr[k];
+              const VrrInstr ib = PR.vrr[two ? k + S : k];
+              const Real a0 = my_vrr[ia.s0], a1 = my_vrr[ia.s1];
+              const Real b0 = my_vrr[ib.s0], b1 = my_vrr[ib.s1];
+              Real ta = cf[kPAx + 3 * ia.kind + ia.dir] * a0;
+              Real tb = cf[kPAx + 3 * ib.kind + ib.dir] * b0;
+              ta = fma(cf[kWPx + 3 * ia.kind + ia.dir], a1, ta);
+              tb = fma(cf[kWPx + 3 * ib.kind + ib.dir], b1, tb);
+              if (ia.n1) ta = fma(h[ia.kind * nh + ia.n1], fma(-cf[kRhoZeta + ia.kind], my_vrr[ia.s3], my_vrr[ia.s2]), ta);
+              if (ib.n1) tb = fma(h[ib.kind * nh + ib.n1], fma(-cf[kRhoZeta + ib.kind], my_vrr[ib.s3], my_vrr[ib.s2]), tb);
+              if (ia.n2) ta = fma(h[2 * nh + ia.n2], my_vrr[ia.s4], ta);
+              if (ib.n2) tb = fma(h[2 * nh + ib.n2], my_vrr[ib.s4], tb);
+              my_vrr[ia.tgt] = ta;
+              if (two) my_vrr[ib.tgt] = tb;
+            }
+          }
+          __syncwarp();
+        }
+        if (active) {
+          for (int k = p.acc_begin + s; k < p.acc_begin + p.nacc; k += S) {
+            const AccInstr a = PR.acc[k];
+            Real w = a.chan == 0 ? Real(1) : cf[kWA + a.chan - 1];
+            my_acc[a.acc] = fma(w, my_vrr[a.slot], my_acc[a.acc]);
+          }
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
   }
   // reduce the group accumulators into group 0's
@@ -693,7 +744,7 @@ __global__ void __launch_bounds__(128, 4) quartet_kernel(DevProgs PR, ClassLaunc
   const ClassProg &p = CL.p;
   unsigned char *wbase = smem_raw + (size_t)warp * CL.smem_per_warp;
   Real *sm = reinterpret_cast<Real *>(wbase);
-  double *gam = reinterpret_cast<double *>(wbase + gamma_offset(p, CL.G, CL.T, sizeof(Real)));
+  double *gam = reinterpret_cast<double *>(wbase + gamma_offset(p, CL.G, CL.T, CL.P, sizeof(Real)));
   for (int it = blockIdx.x * CL.warps + warp; it < T.total; it += gridDim.x * CL.warps) {
     int jb = 0;  // job holding item it (jobs are few; linear search in the parameter block)
     while (jb + 1 < T.njobs && it >= T.j[jb + 1].first) ++jb;
@@ -707,7 +758,7 @@ __global__ void __launch_bounds__(128, 4) quartet_kernel(DevProgs PR, ClassLaunc
     for (int kk = 0; kk < W.nk; ++kk) {
       const int jp = W.k0 + kk;
       const int2 scd = B.pair_sh[jp];
-      Real *acc0 = quartet_block<Real>(B, PR, p, CL.G, CL.T, sm, W.bra, jp, lane);
+      Real *acc0 = quartet_block<Real>(B, PR, p, CL.G, CL.T, CL.P, sm, W.bra, jp, lane);
       const int sh[4] = {sab.x, sab.y, scd.x, scd.y};
       int off[4], n[4];
       for (int t = 0; t < 4; ++t) {
