@@ -369,6 +369,78 @@ __device__ __forceinline__ void stage1(const DevBasis &B, const ClassProg &p, Re
   }
 }
 
+// Vertical recurrence and accumulation of nchunk primitive-table entries,
+// NP per group at a time: group g runs entries r0 + j G + g, j < NP, and each
+// lane applies every step it decodes to all NP of them (NP independent
+// chains per instruction load).  Regions: entry j of group g at
+// work + (j G + g) vrr_size.
+template <typename Real, int NP>
+__device__ __forceinline__ void vrr_multi(const DevProgs &PR, const ClassProg &p, int G, int S, int g, int s,
+                                          int nh, int stride, const Real *ptab, Real *work, Real *my_acc,
+                                          int nchunk) {
+  for (int r0 = 0; r0 < nchunk; r0 += NP * G) {
+    const Real *cf[NP], *h[NP];
+    Real *v[NP];
+    bool act[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const int loc = r0 + j * G + g;
+      act[j] = loc < nchunk;
+      const Real *e = ptab + (act[j] ? loc : r0 + g) * stride;
+      cf[j] = e + p.ltot + 1;
+      h[j] = cf[j] + kNumCoef;
+      v[j] = work + (j * G + g) * p.vrr_size;
+    }
+    if (act[0]) {
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+        for (int t = s; t <= p.ltot + 1; t += S) v[j][t] = t == 0 ? zero_real<Real>() : cf[j][t - 1 - (p.ltot + 1)];
+    }
+    __syncwarp();
+    for (int L = 0; L < p.nvrr_level; ++L) {
+      const int i0 = PR.levels[p.vrr_level0 + L], i1 = PR.levels[p.vrr_level0 + L + 1];
+      if (act[0]) {
+        // steps of one level never read each other's targets, so every
+        // source is read before any target of the level is written; the
+        // optional operands are read only by the steps that use them
+        for (int k = i0 + s; k < i1; k += S) {
+          const VrrInstr in = PR.vrr[k];
+          const int c0 = kPAx + 3 * in.kind + in.dir;
+          Real t[NP];
+#pragma unroll
+          for (int j = 0; j < NP; ++j) t[j] = cf[j][c0] * v[j][in.s0];
+#pragma unroll
+          for (int j = 0; j < NP; ++j) t[j] = fma(cf[j][kWPx - kPAx + c0], v[j][in.s1], t[j]);
+          if (in.n1) {
+            const int hn = in.kind * nh + in.n1, rk = kRhoZeta + in.kind;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) t[j] = fma(h[j][hn], fma(-cf[j][rk], v[j][in.s3], v[j][in.s2]), t[j]);
+          }
+          if (in.n2) {
+            const int hn = 2 * nh + in.n2;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) t[j] = fma(h[j][hn], v[j][in.s4], t[j]);
+          }
+#pragma unroll
+          for (int j = 0; j < NP; ++j) v[j][in.tgt] = t[j];
+        }
+      }
+      __syncwarp();
+    }
+    if (act[0]) {
+      for (int k = p.acc_begin + s; k < p.acc_begin + p.nacc; k += S) {
+        const AccInstr a = PR.acc[k];
+        Real x = my_acc[a.acc];
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+          if (act[j]) x = fma(a.chan == 0 ? Real(1) : cf[j][kWA + a.chan - 1], v[j][a.slot], x);
+        my_acc[a.acc] = x;
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // ------------------------------------------------ one contracted quartet
 // Computes the contracted block(s) of quartet (bra pair ip | ket pair jp) into
 // the warp's shared memory and returns a pointer to the output block (nout
@@ -384,7 +456,6 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
   Real *work = acc0 + p.acc_total;              // VRR regions / HRR slots
   Real *my_acc = accs + (G - 1 - g) * p.acc_total;
   Real *my_vrr = work + g * p.vrr_size;
-  Real *my_vrr2 = work + (G + g) * p.vrr_size;  // the group's second primitive quartet
 
   const int2 sab = B.pair_sh[ip], scd = B.pair_sh[jp];
   const int pp0 = B.pair_pp0[ip], npp = B.pair_npp[ip];
@@ -401,73 +472,19 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
       stage1<Real>(B, p, ptab + lane * stride, ia, ic, sab, scd);
     }
     __syncwarp();
-    // stage 2: recurrences.  P = 2: 2G primitive quartets at a time, group
-    // g running entries r0 + g and r0 + G + g, each lane applying every
-    // step it decodes to both (two independent chains per instruction
-    // load; 5 % faster on the double-float and binary32 classes).  P = 1:
-    // G at a time, each lane taking two steps of one quartet per
-    // iteration (half the vertical regions: the binary64 f classes, bound
-    // by the FP64 pipe, keep their occupancy).
+    // stage 2: recurrences.  P = 2 or 4: PG primitive quartets at a time,
+    // each lane applying every step it decodes to P of them (vrr_multi; two
+    // chains per instruction load measured 5 % faster on the double-float
+    // and binary32 classes than P = 1).  P = 1: G at a time, each lane
+    // taking two steps of one quartet per iteration (the smallest vertical
+    // regions: the binary64 f classes, bound by the FP64 pipe, keep their
+    // occupancy).
     const int nchunk = min(T, npq - c0);
-    if (P == 2) {
-      for (int r0 = 0; r0 < nchunk; r0 += 2 * G) {
-        const int loc = r0 + g, loc2 = r0 + G + g;
-        const bool active = loc < nchunk, active2 = loc2 < nchunk;
-        const Real *e = ptab + loc * stride;
-        const Real *cf = e + p.ltot + 1;
-        const Real *h = cf + kNumCoef;
-        const Real *e2 = ptab + (active2 ? loc2 : loc) * stride;
-        const Real *cf2 = e2 + p.ltot + 1;
-        const Real *h2 = cf2 + kNumCoef;
-        if (active) {
-          for (int t = s; t <= p.ltot + 1; t += S) my_vrr[t] = t == 0 ? zero_real<Real>() : e[t - 1];
-          for (int t = s; t <= p.ltot + 1; t += S) my_vrr2[t] = t == 0 ? zero_real<Real>() : e2[t - 1];
-        }
-        __syncwarp();
-        for (int L = 0; L < p.nvrr_level; ++L) {
-          const int i0 = PR.levels[p.vrr_level0 + L], i1 = PR.levels[p.vrr_level0 + L + 1];
-          if (active) {
-            // steps of one level never read each other's targets, so every
-            // source is read before any target of the level is written; the
-            // optional operands are read only by the steps that use them (four
-            // steps of one quartet per iteration and eight-output digestion
-            // groups measured 1-3 % slower)
-            for (int k = i0 + s; k < i1; k += S) {
-              const VrrInstr ia = PR.vrr[k];
-              const int c0 = kPAx + 3 * ia.kind + ia.dir;
-              Real ta = cf[c0] * my_vrr[ia.s0];
-              Real tb = cf2[c0] * my_vrr2[ia.s0];
-              ta = fma(cf[kWPx - kPAx + c0], my_vrr[ia.s1], ta);
-              tb = fma(cf2[kWPx - kPAx + c0], my_vrr2[ia.s1], tb);
-              if (ia.n1) {
-                const int hn = ia.kind * nh + ia.n1, rk = kRhoZeta + ia.kind;
-                ta = fma(h[hn], fma(-cf[rk], my_vrr[ia.s3], my_vrr[ia.s2]), ta);
-                tb = fma(h2[hn], fma(-cf2[rk], my_vrr2[ia.s3], my_vrr2[ia.s2]), tb);
-              }
-              if (ia.n2) {
-                ta = fma(h[2 * nh + ia.n2], my_vrr[ia.s4], ta);
-                tb = fma(h2[2 * nh + ia.n2], my_vrr2[ia.s4], tb);
-              }
-              my_vrr[ia.tgt] = ta;
-              my_vrr2[ia.tgt] = tb;
-            }
-          }
-          __syncwarp();
-        }
-        if (active) {
-          for (int k = p.acc_begin + s; k < p.acc_begin + p.nacc; k += S) {
-            const AccInstr a = PR.acc[k];
-            Real w = a.chan == 0 ? Real(1) : cf[kWA + a.chan - 1];
-            Real v = fma(w, my_vrr[a.slot], my_acc[a.acc]);
-            if (active2) {
-              Real w2 = a.chan == 0 ? Real(1) : cf2[kWA + a.chan - 1];
-              v = fma(w2, my_vrr2[a.slot], v);
-            }
-            my_acc[a.acc] = v;
-          }
-        }
-        __syncwarp();
-      }
+    if (P > 1) {
+      if (P == 4)
+        vrr_multi<Real, 4>(PR, p, G, S, g, s, nh, stride, ptab, work, my_acc, nchunk);
+      else
+        vrr_multi<Real, 2>(PR, p, G, S, g, s, nh, stride, ptab, work, my_acc, nchunk);
     } else {
       for (int r0 = 0; r0 < nchunk; r0 += G) {
         const int loc = r0 + g;
