@@ -254,7 +254,17 @@ ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
     best.smem_per_warp = (int)warp_smem_bytes(p, 1, 8, 1, real_bytes);
   }
   best.warps = std::max(1, std::min(4, kSmemBudget / std::max(best.smem_per_warp, 1)));
+  best.split = 1;
   return best;
+}
+
+// Layout of a derivative class in the gradient: as make_launch, and for the
+// classes whose J/K build is class-specialised (work items of up to
+// kGenKetChunk kets, one per lane there) one warp per ket of an item.
+ClassLaunch grad_launch(const ClassProg &p, size_t real_bytes) {
+  ClassLaunch cl = make_launch(p, real_bytes);
+  if (gen_class(p.la, p.lb, p.lc, p.ld)) cl.split = kGenKetChunk;
+  return cl;
 }
 
 // Warps per CTA that put the most warps on an SM, given the shared memory one
@@ -288,12 +298,14 @@ int launch_class(const DevProgs &PR, const ClassLaunch &cl_in, const JobTable &T
     regs.store(fa.numRegs > 0 ? fa.numRegs : 128);
   }
   ClassLaunch cl = cl_in;
+  cl.split = std::max(cl.split, 1);
   cl.warps = warps_per_cta(cl.smem_per_warp, regs.load());
   const size_t smem = (size_t)cl.smem_per_warp * cl.warps;
   if (smem > (size_t)kMaxSmem)
     return set_error(LTJK_EUNSUPPORTED, "class (%d%d|%d%d) needs %zu bytes of shared memory",
                      cl.p.la, cl.p.lb, cl.p.lc, cl.p.ld, smem);
-  const int grid = (T.total + cl.warps - 1) / cl.warps;  // one warp per item, not persistent
+  const long long units = (long long)T.total * std::max(cl.split, 1);
+  const int grid = (int)((units + cl.warps - 1) / cl.warps);  // one warp per unit, not persistent
   quartet_kernel<Real, MODE><<<grid, 32 * cl.warps, smem, st>>>(PR, cl, T);
   CUDA_TRY(cudaGetLastError());
   g_launches += 1;
@@ -755,15 +767,15 @@ int launch_classes(ltjk_ctx *ctx, const JKArgs &a, cudaStream_t st) {
       if (MODE == kJK)
         rc = ieee ? launch_jk<double>(p, ctx->progs, T, s2) : launch_jk<dflt>(p, ctx->progs, T, s2);
       else
-        rc = ieee ? launch_class<double, MODE>(ctx->progs, make_launch(p, sizeof(double)), T, s2)
-                  : launch_class<dflt, MODE>(ctx->progs, make_launch(p, sizeof(dflt)), T, s2);
+        rc = ieee ? launch_class<double, MODE>(ctx->progs, grad_launch(p, sizeof(double)), T, s2)
+                  : launch_class<dflt, MODE>(ctx->progs, grad_launch(p, sizeof(dflt)), T, s2);
       if (rc) return rc;
     }
     if (w->n32) {
       cudaStream_t s2 = ctx->side[next++ % kSideStreams];
       const JobTable T = single_job(B, a, w->items32.as<WorkItem>(), w->n32);
       rc = MODE == kJK ? launch_jk<float>(p, ctx->progs, T, s2)
-                       : launch_class<float, MODE>(ctx->progs, make_launch(p, sizeof(float)), T, s2);
+                       : launch_class<float, MODE>(ctx->progs, grad_launch(p, sizeof(float)), T, s2);
       if (rc) return rc;
     }
   }

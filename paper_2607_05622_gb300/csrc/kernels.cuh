@@ -225,6 +225,7 @@ struct ClassLaunch {
   int smem_per_warp;  // bytes
   int T;        // primitive-table entries (set-up of T primitive quartets at a time)
   int P;        // primitive quartets per group in the vertical recurrence (1 or 2)
+  int split;    // warps per work item: warp sub takes kets sub, sub + split, ...
 };
 
 // The digestion tabulates its output offsets in the dead primitive table: ten
@@ -762,7 +763,9 @@ __global__ void __launch_bounds__(128, 4) quartet_kernel(DevProgs PR, ClassLaunc
   unsigned char *wbase = smem_raw + (size_t)warp * CL.smem_per_warp;
   Real *sm = reinterpret_cast<Real *>(wbase);
   double *gam = reinterpret_cast<double *>(wbase + gamma_offset(p, CL.G, CL.T, CL.P, sizeof(Real)));
-  for (int it = blockIdx.x * CL.warps + warp; it < T.total; it += gridDim.x * CL.warps) {
+  const long long units = (long long)T.total * CL.split;
+  for (long long u = (long long)blockIdx.x * CL.warps + warp; u < units; u += (long long)gridDim.x * CL.warps) {
+    const int it = (int)(u / CL.split), sub = (int)(u % CL.split);
     int jb = 0;  // job holding item it (jobs are few; linear search in the parameter block)
     while (jb + 1 < T.njobs && it >= T.j[jb + 1].first) ++jb;
     const JobDesc &J = T.j[jb];
@@ -772,7 +775,7 @@ __global__ void __launch_bounds__(128, 4) quartet_kernel(DevProgs PR, ClassLaunc
     const int li = it - J.first;
     const WorkItem W = J.items[li];
     const int2 sab = B.pair_sh[W.bra];
-    for (int kk = 0; kk < W.nk; ++kk) {
+    for (int kk = sub; kk < W.nk; kk += CL.split) {
       const int jp = W.k0 + kk;
       const int2 scd = B.pair_sh[jp];
       Real *acc0 = quartet_block<Real>(B, PR, p, CL.G, CL.T, CL.P, sm, W.bra, jp, lane);

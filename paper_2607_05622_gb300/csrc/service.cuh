@@ -151,11 +151,11 @@ int ltjk_service::step(std::vector<SvcJob *> &run, const StreamSet &S, int cap) 
               launch_jk<double>(*prog, PR, T, st);
           } else {
             if (prec == 0)
-              launch_class<dflt, kGrad>(PR, make_launch(*prog, sizeof(dflt)), T, st);
+              launch_class<dflt, kGrad>(PR, grad_launch(*prog, sizeof(dflt)), T, st);
             else if (prec == 1)
-              launch_class<float, kGrad>(PR, make_launch(*prog, sizeof(float)), T, st);
+              launch_class<float, kGrad>(PR, grad_launch(*prog, sizeof(float)), T, st);
             else
-              launch_class<double, kGrad>(PR, make_launch(*prog, sizeof(double)), T, st);
+              launch_class<double, kGrad>(PR, grad_launch(*prog, sizeof(double)), T, st);
           }
           ++nl;
           T.njobs = 0;
