@@ -394,7 +394,6 @@ struct ltjk_ctx {
   const double *boys = nullptr;
   const float2 *boys2 = nullptr;
   std::vector<std::unique_ptr<ClassWork>> work;       // value build
-  std::vector<std::unique_ptr<ClassWork>> work_grad;  // gradient (same screening)
   DevBuf scratch;
   DevBuf d_sph;   // Cartesian -> real-spherical matrix T [nsph][nao], built on first use
   int nsph = 0;
@@ -574,7 +573,6 @@ int build_work(ltjk_ctx &c) {
   const bool mixed = c.opts.precision == LTJK_MIXED;
   const double tmix = c.opts.mixed_tau;
   c.work.clear();
-  c.work_grad.clear();
   c.stats.quartets_total = 0;
   c.stats.quartets_kept = 0;
   c.stats.quartets_fp64 = 0;
