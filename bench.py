@@ -525,7 +525,7 @@ def run_gpu(args, world, rank, local):
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
     hC, hV, he, hv, hX = pin(w.C_occ), pin(w.C_vir), pin(w.eps_occ), pin(w.eps_vir), pin(w.X)
     hJ = torch.empty((nd, N, N), dtype=torch.float64).pin_memory()
-    hK = torch.empty_like(hJ)
+    hK = torch.empty((nd, N, N), dtype=torch.float64).pin_memory()  # (empty_like would not pin)
     h2d = sum(x.numel() * 8 for x in (hC, hV, he, hv, hX))
     d2h = 2 * nd * N * N * 8
 
