@@ -396,7 +396,7 @@ void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv
     T.nout = (int)final_instr.size();
     T.a0 = a_lo;
     T.na = a_hi - a_lo;
-    T.store_off = dtile < 0 ? a_lo * blk : dtile * P.nout;
+    T.store_off = (dtile < 0 ? 0 : dtile * P.nout) + a_lo * blk;
     const int nodes_end = hg.acc_total + (int)hg.level.size();  // first output node
     if (nodes_end + T.nout > 65000) throw std::runtime_error("HRR output block too large");
     for (size_t k = 0; k < final_instr.size(); ++k) {
@@ -449,17 +449,16 @@ void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv
     out.flops = hg.flops;
     return out;
   };
-  std::vector<Tile> tiles;
-  if (deriv) {
-    for (int t = 0; t < 9; ++t) tiles.push_back(make_tile(t, 0, ncart(la)));
-  } else {
-    // fewest a-ranges whose tiles fit: the class's slots (accumulators and
-    // the larger of the vertical region and the tile's horizontal region)
-    // within kTileSlotBudget, or, where the accumulators and the vertical
-    // region alone exceed it, a horizontal region no larger than the
-    // vertical one; one component per tile is the last resort
-    const int na = ncart(la);
-    const int limit = std::max(kTileSlotBudget, P.acc_total + P.vrr_size);
+  // The fewest a-ranges whose tiles fit: plain integrals keep the class's
+  // slots (accumulators and the larger of the vertical region and the tile's
+  // horizontal region) within kTileSlotBudget, or, where the accumulators
+  // and the vertical region alone exceed it, a horizontal region no larger
+  // than the vertical one; every tile must fit the 16-bit slot indices (the
+  // derivative tiles of the f classes split for that alone).  One component
+  // per tile is the last resort.
+  const int na = ncart(la);
+  const int limit = deriv ? 1 << 30 : std::max(kTileSlotBudget, P.acc_total + P.vrr_size);
+  auto ranged = [&](int dtile) {
     for (int nt = 1; nt <= na; ++nt) {
       const int chunk = (na + nt - 1) / nt;
       if (nt > 1 && (na + chunk - 1) / chunk != nt) continue;  // same ranges as a smaller count
@@ -467,21 +466,26 @@ void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv
       bool fits = true;
       try {
         for (int a0 = 0; a0 < na; a0 += chunk) {
-          cand.push_back(make_tile(-1, a0, std::min(na, a0 + chunk)));
+          cand.push_back(make_tile(dtile, a0, std::min(na, a0 + chunk)));
           if (P.acc_total + std::max(P.vrr_size, cand.back().T.hrr_size) > limit) {
             fits = false;
-            if (chunk > 1) break;  // try more tiles; one component per tile is the last resort
+            if (chunk > 1) break;  // try more tiles
           }
         }
       } catch (const std::runtime_error &) {
         if (chunk == 1) throw;
         fits = false;
       }
-      if (fits || chunk == 1) {
-        tiles = std::move(cand);
-        break;
-      }
+      if (fits || chunk == 1) return cand;
     }
+    return std::vector<Tile>();
+  };
+  std::vector<Tile> tiles;
+  if (deriv) {
+    for (int t = 0; t < 9; ++t)
+      for (Tile &x : ranged(t)) tiles.push_back(std::move(x));
+  } else {
+    tiles = ranged(-1);
   }
   P.ntile = (int)tiles.size();
   P.tile_begin = (int)ps.tiles.size();
@@ -561,17 +565,21 @@ static void validate(const ProgramSet &ps, const ClassProg &P) {
     if (T.out_base + T.nout > hmax) bad("output block");
     const int blk = P.nout / ncart(P.la);
     if (T.na < 1 || T.a0 < 0 || T.a0 + T.na > ncart(P.la) || T.nout != T.na * blk) bad("tile range");
-    if (P.deriv ? (T.na != ncart(P.la) || T.store_off != t * P.nout) : T.store_off != T.a0 * blk)
-      bad("tile store offset");
+    const int comp = T.store_off / P.nout;  // derivative component (centre, direction); 0 for values
+    if (T.store_off != comp * P.nout + T.a0 * blk || comp > (P.deriv ? 8 : 0)) bad("tile store offset");
   }
-  if (!P.deriv) {  // value tiles cover the a components in order
-    int next = 0;
+  {  // the tiles of each component cover the a components in order
+    int comp = 0, next = 0;
     for (int t = 0; t < P.ntile; ++t) {
       const TileProg &T = ps.tiles[P.tile_begin + t];
-      if (T.a0 != next) bad("value tiles out of order");
+      if (next == ncart(P.la)) {
+        ++comp;
+        next = 0;
+      }
+      if (T.store_off / P.nout != comp || T.a0 != next) bad("tiles out of order");
       next += T.na;
     }
-    if (next != ncart(P.la)) bad("value tiles do not cover the block");
+    if (next != ncart(P.la) || comp != (P.deriv ? 8 : 0)) bad("tiles do not cover the block");
   }
 }
 
