@@ -33,9 +33,7 @@ std::atomic<unsigned long long> g_launches{0};  // kernels launched by this libr
 constexpr int kKetChunk = 1;  // ket pairs per work item of the interpreted kernel: one quartet per
                               // warp balances best (16 per item measured 4-5 % slower)
 constexpr int kGenKetChunk = 32;         // most ket pairs per work item (class-specialised kernel)
-constexpr long long kTargetItems = 152 * 8;  // work items a class should offer the GPU (before
-                                             // its items of the specialised kernel fill 32 lanes;
-                                             // 152 x 24 measured 2 % slower in mixed precision)
+constexpr long long kTargetItems = 152 * 24;  // work items a class should offer the GPU
 constexpr int kSideStreams = 4;          // class launches of one build run on these concurrently
 constexpr int kSmemBudget = 200 * 1024;  // bytes of shared memory per CTA we plan for
 constexpr int kMaxSmem = 227 * 1024;
