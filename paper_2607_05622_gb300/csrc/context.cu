@@ -198,14 +198,14 @@ int device_programs(int dev, DevProgs *out, const double **boys, const float2 **
 // Launch configuration of one class program: groups per warp from the average
 // width of a recurrence level, warps per CTA from the shared-memory budget.
 ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
-  // Candidate layouts: G groups of S lanes, each group running P = 4, 2 or 1
+  // Candidate layouts: G groups of S lanes, each group running P = 2 or 1
   // primitive quartets (its S lanes over the independent steps of each
   // recurrence level), and a T-entry primitive table (PG <= T; T shrinks
   // from 32 while the warp's shared memory would keep fewer than 16 warps on
   // an SM, as long as the digestion's offset table still fits in it).  Cost
   // per primitive quartet, in warp iterations: sum over levels of
-  // ceil(width / S) x S / (32 P) for P = 4, 2 (one step per lane per
-  // iteration, applied to P quartets) or ceil(width / 2S) x S / 32 for P = 1 (two
+  // ceil(width / S) x S / 64 for P = 2 (one step per lane per iteration,
+  // applied to two quartets) or ceil(width / 2S) x S / 32 for P = 1 (two
   // steps of one quartet per lane per iteration), scaled by
   // 16 / (warps per SM) when shared memory allows fewer than 16 warps (a
   // target of 12 measured 1 % slower, 8 measured 13 % slower).  The
@@ -214,7 +214,7 @@ ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
   const ProgramSet &ps = g_prog.ps;
   ClassLaunch best{};
   double best_cost = 1e300;
-  for (int P = 2; P >= 1; P /= 2)
+  for (int P = 2; P >= 1; --P)
   for (int S = 32; S >= 1; S /= 2) {
     if (P * (32 / S) > 32) continue;  // the table holds 32 entries: PG of them in flight
     ClassLaunch cl{};
@@ -232,7 +232,7 @@ ClassLaunch make_launch(const ClassProg &p, size_t real_bytes) {
     double cost = 0.0;
     for (int L = 0; L < p.nvrr_level; ++L) {
       const int w = ps.levels[p.vrr_level0 + L + 1] - ps.levels[p.vrr_level0 + L];
-      cost += P > 1 ? (double)((w + S - 1) / S) * S / (32.0 * P) : (double)((w + 2 * S - 1) / (2 * S)) * S / 32.0;
+      cost += P == 2 ? (double)((w + S - 1) / S) * S / 64.0 : (double)((w + 2 * S - 1) / (2 * S)) * S / 32.0;
     }
     cost += 1.0 / 32.0;  // per-quartet overheads: set-up share, syncs
     // P = 1 loads each step's instruction for one quartet only: weighted by

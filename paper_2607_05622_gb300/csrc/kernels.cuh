@@ -473,19 +473,16 @@ __device__ Real *quartet_block(const DevBasis &B, const DevProgs &PR, const Clas
       stage1<Real>(B, p, ptab + lane * stride, ia, ic, sab, scd);
     }
     __syncwarp();
-    // stage 2: recurrences.  P = 2 or 4: PG primitive quartets at a time,
-    // each lane applying every step it decodes to P of them (vrr_multi; two
+    // stage 2: recurrences.  P = 2: 2G primitive quartets at a time, each
+    // lane applying every step it decodes to two of them (vrr_multi; two
     // chains per instruction load measured 5 % faster on the double-float
-    // and binary32 classes than P = 1).  P = 1: G at a time, each lane
-    // taking two steps of one quartet per iteration (the smallest vertical
-    // regions: the binary64 f classes, bound by the FP64 pipe, keep their
-    // occupancy).
+    // and binary32 classes than P = 1, four chains 2 % slower than two).
+    // P = 1: G at a time, each lane taking two steps of one quartet per
+    // iteration (the smallest vertical regions: the binary64 f classes,
+    // bound by the FP64 pipe, keep their occupancy).
     const int nchunk = min(T, npq - c0);
-    if (P > 1) {
-      if (P == 4)
-        vrr_multi<Real, 4>(PR, p, G, S, g, s, nh, stride, ptab, work, my_acc, nchunk);
-      else
-        vrr_multi<Real, 2>(PR, p, G, S, g, s, nh, stride, ptab, work, my_acc, nchunk);
+    if (P == 2) {
+      vrr_multi<Real, 2>(PR, p, G, S, g, s, nh, stride, ptab, work, my_acc, nchunk);
     } else {
       for (int r0 = 0; r0 < nchunk; r0 += G) {
         const int loc = r0 + g;
