@@ -153,6 +153,10 @@ LTJK_HD constexpr bool ieee64_class(int la, int lb, int lc, int ld) {
 
 void build_programs(ProgramSet &ps);
 void build_one_program(ProgramSet &ps, int la, int lb, int lc, int ld, int deriv, ClassProg &out);
+// The checks build_programs applies to every program (slots in range, no
+// level writing a slot it reads, tiles covering the block), for a program
+// built on its own; throws std::runtime_error.
+void validate_program(const ProgramSet &ps, const ClassProg &P);
 // Straight-line C++/CUDA source of one class program (codegen.cpp).
 std::string emit_class_source(const ProgramSet &ps, int la, int lb, int lc, int ld, int deriv,
                               const std::string &prefix);

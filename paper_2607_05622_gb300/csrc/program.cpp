@@ -583,6 +583,8 @@ static void validate(const ProgramSet &ps, const ClassProg &P) {
   }
 }
 
+void validate_program(const ProgramSet &ps, const ClassProg &P) { validate(ps, P); }
+
 void build_programs(ProgramSet &ps) {
   ps = ProgramSet{};
   ps.progs.resize(2 * kNumPairClass * kNumPairClass);

@@ -9,6 +9,7 @@
 // the straight-line source the class generator emits.  Compiled by the tests
 // themselves (g++), never by the library build.
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <vector>
 
@@ -123,11 +124,8 @@ void setup_primitive(const ClassProg &p, const R *A, const R *B, const R *C, con
 namespace {
 
 template <typename R>
-int quartet_t(int la, int lb, int lc, int ld, int deriv, const double *ctr_d, const int *np,
-              const double *exps_d, const double *coefs_d, double *out) {
-  const ProgramSet &ps = programs();
-  if (la < lb || lc < ld) return -1;
-  const ClassProg &p = ps.progs[quartet_index(la, lb, lc, ld, deriv)];
+int quartet_pt(const ProgramSet &ps, const ClassProg &p, const double *ctr_d, const int *np,
+               const double *exps_d, const double *coefs_d, double *out) {
   int nprim = 0;
   for (int s = 0; s < 4; ++s) nprim += np[s];
   const std::vector<R> ctr(ctr_d, ctr_d + 12), exps(exps_d, exps_d + nprim), coefs(coefs_d, coefs_d + nprim);
@@ -176,7 +174,41 @@ int quartet_t(int la, int lb, int lc, int ld, int deriv, const double *ctr_d, co
   return 0;
 }
 
+template <typename R>
+int quartet_t(int la, int lb, int lc, int ld, int deriv, const double *ctr_d, const int *np,
+              const double *exps_d, const double *coefs_d, double *out) {
+  const ProgramSet &ps = programs();
+  if (la < lb || lc < ld) return -1;
+  return quartet_pt<R>(ps, ps.progs[quartet_index(la, lb, lc, ld, deriv)], ctr_d, np, exps_d, coefs_d, out);
+}
+
 }  // namespace
+
+// Derivative programs of classes with an f shell, which the library does not
+// generate (its gradient stops at d): built here one class at a time with the
+// library's generator and validated by its checks, then interpreted as above
+// in binary64.  *ntile receives the class's tile count (nine (centre,
+// direction) tiles, each split over ranges of a's components where it
+// would overflow the 16-bit slots).  out as pe_quartet_d with deriv = 1.
+extern "C" int pe_quartet_fderiv(int la, int lb, int lc, int ld, const double *ctr, const int *np,
+                                 const double *exps, const double *coefs, double *out, int *ntile) {
+  if (la < lb || lc < ld) return -1;
+  static std::map<int, std::pair<ProgramSet, ClassProg>> cache;
+  const int key = ((la * 4 + lb) * 4 + lc) * 4 + ld;
+  auto it = cache.find(key);
+  if (it == cache.end()) {
+    std::pair<ProgramSet, ClassProg> e;
+    try {
+      build_one_program(e.first, la, lb, lc, ld, 1, e.second);
+      validate_program(e.first, e.second);
+    } catch (...) {
+      return -2;
+    }
+    it = cache.emplace(key, std::move(e)).first;
+  }
+  *ntile = it->second.second.ntile;
+  return quartet_pt<double>(it->second.first, it->second.second, ctr, np, exps, coefs, out);
+}
 
 extern "C" int pe_quartet_d(int la, int lb, int lc, int ld, int deriv, const double *ctr, const int *np,
                             const double *exps, const double *coefs, double *out) {

@@ -200,3 +200,59 @@ def test_every_derivative_class_against_finite_differences(pe, oracle):
                     assert err <= 1e-6 * np.abs(fd).max(), ((la, lb, lc, ld), centre, x, err)
             checked += 1
     assert checked == 36
+
+
+def test_f_derivative_programs_against_finite_differences(pe, oracle):
+    """The generator's derivative programs of f classes (not used by the
+    library, whose gradient stops at d; built here class by class and
+    validated by the generator's checks): the nine (centre, direction) tiles
+    equal central differences of the oracle's value blocks, including
+    (ff|ff), whose (centre, direction) tiles split over ranges of a's
+    components to fit the 16-bit slots."""
+    rng = np.random.default_rng(12)
+    coords = [np.zeros(3)]
+    while len(coords) < 4:  # four atoms 1.3 to 2.6 bohr apart, in 3D
+        p = coords[-1] + rng.normal(size=3)
+        d = min(np.linalg.norm(p - q) for q in coords)
+        if 1.3 <= d <= 2.6:
+            coords.append(p)
+    mol = W.build_molecule([tuple(c) for c in coords], ["heavy_tz"] * 4,
+                           W.draw_tz_bases(np.random.default_rng(8)))
+    off = np.concatenate([[0], np.cumsum(mol.shell_nprim)])
+    first = {}
+    for s, (a, l) in enumerate(zip(mol.shell_atom, mol.shell_l)):
+        key, lo = (int(a), int(l)), mol.exps[off[s]:off[s + 1]].min()
+        if key not in first or lo < first[key][1]:
+            first[key] = (s, lo)
+    cn = oracle.norm_coefs(mol)
+    P = ctypes.POINTER(ctypes.c_double)
+    h = 1e-4
+    tiles = {}
+    for cls in [(3, 0, 0, 0), (3, 1, 1, 0), (2, 1, 3, 0), (3, 2, 2, 0), (3, 3, 0, 0), (3, 3, 3, 3)]:
+        pick = [first[(atom, l)][0] for atom, l in enumerate(cls)]
+        ls = list(cls)
+        ctr = np.concatenate([mol.coords[mol.shell_atom[s]] for s in pick]).astype(np.float64)
+        np_ = np.array([mol.shell_nprim[s] for s in pick], dtype=np.int32)
+        ex = np.concatenate([mol.exps[off[s]:off[s + 1]] for s in pick])
+        co = np.concatenate([cn[off[s]:off[s + 1]] for s in pick])
+        n = [(l + 1) * (l + 2) // 2 for l in ls]
+        out = np.zeros(9 * int(np.prod(n)))
+        nt = ctypes.c_int(0)
+        rc = pe.pe_quartet_fderiv(*ls, ctr.ctypes.data_as(P), np_.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  ex.ctypes.data_as(P), co.ctypes.data_as(P), out.ctypes.data_as(P),
+                                  ctypes.byref(nt))
+        assert rc == 0, cls
+        tiles[cls] = nt.value
+        got = out.reshape([9] + n)
+        for centre in range(3):
+            for x in range(3):
+                blocks = []
+                for sgn in (1.0, -1.0):
+                    cc = mol.coords.copy()
+                    cc[centre, x] += sgn * h
+                    blocks.append(oracle.shell_quartet(mol.with_coords(cc), *pick))
+                fd = (blocks[0] - blocks[1]) / (2 * h)
+                err = np.abs(got[3 * centre + x] - fd).max()
+                assert np.abs(fd).max() > 1e-5, (cls, centre, x)
+                assert err <= 1e-6 * np.abs(fd).max(), (cls, centre, x, err / np.abs(fd).max())
+    assert tiles[(3, 0, 0, 0)] == 9 and tiles[(3, 3, 3, 3)] > 9, tiles
