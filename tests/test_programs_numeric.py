@@ -8,7 +8,9 @@ the programs run in long double, 1e-8 in binary64, whose rounding the f
 blocks' horizontal recurrence amplifies); and the derivative programs' nine
 tiles, every class, against central differences of the oracle's blocks: the generator's
 vertical and horizontal steps, its compacted slots, channel weights and
-component order are right before any kernel runs them."""
+component order are right before any kernel runs them.  The derivative
+programs of f classes, which the library does not use yet, are checked the
+same way against central differences, (ff|ff) with its sub-tiles."""
 import ctypes
 import os
 import shutil
