@@ -189,9 +189,12 @@ int quartet_t(int la, int lb, int lc, int ld, int deriv, const double *ctr_d, co
 // library's generator and validated by its checks, then interpreted as above
 // in binary64.  *ntile receives the class's tile count (nine (centre,
 // direction) tiles, each split over ranges of a's components where it
-// would overflow the 16-bit slots).  out as pe_quartet_d with deriv = 1.
-extern "C" int pe_quartet_fderiv(int la, int lb, int lc, int ld, const double *ctr, const int *np,
-                                 const double *exps, const double *coefs, double *out, int *ntile) {
+// would overflow the 16-bit slots).  out as pe_quartet_d with deriv = 1;
+// pe_quartet_fderiv_ld runs the same program in long double.
+namespace {
+template <typename R>
+int fderiv_t(int la, int lb, int lc, int ld, const double *ctr, const int *np,
+             const double *exps, const double *coefs, double *out, int *ntile) {
   if (la < lb || lc < ld) return -1;
   static std::map<int, std::pair<ProgramSet, ClassProg>> cache;
   const int key = ((la * 4 + lb) * 4 + lc) * 4 + ld;
@@ -207,7 +210,18 @@ extern "C" int pe_quartet_fderiv(int la, int lb, int lc, int ld, const double *c
     it = cache.emplace(key, std::move(e)).first;
   }
   *ntile = it->second.second.ntile;
-  return quartet_pt<double>(it->second.first, it->second.second, ctr, np, exps, coefs, out);
+  return quartet_pt<R>(it->second.first, it->second.second, ctr, np, exps, coefs, out);
+}
+}  // namespace
+
+extern "C" int pe_quartet_fderiv(int la, int lb, int lc, int ld, const double *ctr, const int *np,
+                                 const double *exps, const double *coefs, double *out, int *ntile) {
+  return fderiv_t<double>(la, lb, lc, ld, ctr, np, exps, coefs, out, ntile);
+}
+
+extern "C" int pe_quartet_fderiv_ld(int la, int lb, int lc, int ld, const double *ctr, const int *np,
+                                    const double *exps, const double *coefs, double *out, int *ntile) {
+  return fderiv_t<long double>(la, lb, lc, ld, ctr, np, exps, coefs, out, ntile);
 }
 
 extern "C" int pe_quartet_d(int la, int lb, int lc, int ld, int deriv, const double *ctr, const int *np,

@@ -258,3 +258,82 @@ def test_f_derivative_programs_against_finite_differences(pe, oracle):
                 assert np.abs(fd).max() > 1e-5, (cls, centre, x)
                 assert err <= 1e-6 * np.abs(fd).max(), (cls, centre, x, err / np.abs(fd).max())
     assert tiles[(3, 0, 0, 0)] == 9 and tiles[(3, 3, 3, 3)] > 9, tiles
+
+
+def _cart(l):
+    return [(lx, ly, l - lx - ly) for lx in range(l, -1, -1) for ly in range(l - lx, -1, -1)]
+
+
+def _exact_derivative_tiles(oracle, mol, cn, shells):
+    """d/dA_x, d/dB_x, d/dC_x of a contracted block from the oracle's
+    primitive integrals over raw Gaussians, by the rule d/dA g_a = 2 alpha
+    g_{a+1} - a_x g_{a-1} (the centre of each shell moves with it)."""
+    ls = [int(mol.shell_l[s]) for s in shells]
+    n = [(l + 1) * (l + 2) // 2 for l in ls]
+    off = np.concatenate([[0], np.cumsum(mol.shell_nprim)])
+    X = [mol.coords[mol.shell_atom[s]] for s in shells]
+    out = np.zeros([9] + n)
+    for centre in range(3):
+        l = ls[centre]
+        up_l, dn_l = _cart(l + 1), (_cart(l - 1) if l > 0 else [])
+        for x in range(3):
+            raise_i = np.array([up_l.index(tuple(c[t] + (t == x) for t in range(3))) for c in _cart(l)])
+            pw = np.array([c[x] for c in _cart(l)], dtype=float)
+            lower_i = np.array([dn_l.index(tuple(c[t] - (t == x) for t in range(3))) if c[x] else 0
+                                for c in _cart(l)])
+            for i in range(off[shells[0]], off[shells[0] + 1]):
+                for j in range(off[shells[1]], off[shells[1] + 1]):
+                    for k in range(off[shells[2]], off[shells[2] + 1]):
+                        for m in range(off[shells[3]], off[shells[3] + 1]):
+                            e = [mol.exps[i], mol.exps[j], mol.exps[k], mol.exps[m]]
+                            w = cn[i] * cn[j] * cn[k] * cn[m]
+                            Lu = list(ls); Lu[centre] += 1
+                            blk = 2 * e[centre] * np.take(oracle.eri_prim(Lu, e, X), raise_i, axis=centre)
+                            if l > 0:
+                                Ld = list(ls); Ld[centre] -= 1
+                                dn = np.take(oracle.eri_prim(Ld, e, X), lower_i, axis=centre)
+                                shape = [1, 1, 1, 1]; shape[centre] = len(pw)
+                                blk = blk - pw.reshape(shape) * dn
+                            out[3 * centre + x] += w * blk
+    return out
+
+
+def test_f_derivative_programs_against_exact_derivatives(pe, oracle):
+    """The f-class derivative programs against derivative blocks assembled
+    from the oracle's primitive integrals with the Gaussian derivative rule:
+    run in long double they agree to 1e-11 of the block's largest element (a
+    far tighter pin than the finite differences); in binary64 the deep f
+    recurrences lose digits to cancellation, as the value classes do, and
+    the gate there is 1e-8."""
+    rng = np.random.default_rng(13)
+    coords = [np.zeros(3)]
+    while len(coords) < 4:
+        p = coords[-1] + rng.normal(size=3)
+        d = min(np.linalg.norm(p - q) for q in coords)
+        if 1.3 <= d <= 2.6:
+            coords.append(p)
+    mol = W.build_molecule([tuple(c) for c in coords], ["heavy_tz"] * 4,
+                           W.draw_tz_bases(np.random.default_rng(9)))
+    off = np.concatenate([[0], np.cumsum(mol.shell_nprim)])
+    first = {}
+    for s, (a, l) in enumerate(zip(mol.shell_atom, mol.shell_l)):
+        key, lo = (int(a), int(l)), mol.exps[off[s]:off[s + 1]].min()
+        if key not in first or lo < first[key][1]:
+            first[key] = (s, lo)
+    cn = oracle.norm_coefs(mol)
+    P = ctypes.POINTER(ctypes.c_double)
+    for cls in [(3, 0, 1, 0), (3, 2, 2, 1), (2, 1, 3, 1)]:
+        pick = [first[(atom, l)][0] for atom, l in enumerate(cls)]
+        ctr = np.concatenate([mol.coords[mol.shell_atom[s]] for s in pick]).astype(np.float64)
+        np_ = np.array([mol.shell_nprim[s] for s in pick], dtype=np.int32)
+        ex = np.concatenate([mol.exps[off[s]:off[s + 1]] for s in pick])
+        co = np.concatenate([cn[off[s]:off[s + 1]] for s in pick])
+        n = [(l + 1) * (l + 2) // 2 for l in cls]
+        ref = _exact_derivative_tiles(oracle, mol, cn, pick)
+        for fn, tol in ((pe.pe_quartet_fderiv_ld, 1e-11), (pe.pe_quartet_fderiv, 1e-8)):
+            out = np.zeros(9 * int(np.prod(n)))
+            nt = ctypes.c_int(0)
+            assert fn(*cls, ctr.ctypes.data_as(P), np_.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                      ex.ctypes.data_as(P), co.ctypes.data_as(P), out.ctypes.data_as(P), ctypes.byref(nt)) == 0
+            err = np.abs(out.reshape([9] + n) - ref).max() / np.abs(ref).max()
+            assert err <= tol, (cls, fn.__name__, err)
