@@ -25,6 +25,13 @@ EPS32 = 1e-2
 # element (an f x f density block), plus the rounding of D: gamma_104 with
 # u = 2^-24.
 EPS_DIG = 104 * 2.0 ** -24
+# A digestion of the binary32 quartets on tensor cores in TF32 (not built):
+# each operand (integral, density) truncated to TF32's 10 explicit bits,
+# relative error below u = 2^-10; the product of two TF32 values is exact in
+# binary32 and the accumulation is binary32, so the operand rounding adds
+# (1 + u)^2 - 1 = 2u + u^2 per product, and the binary32 sums stay within
+# EPS_DIG as long as each accumulation chain has at most 100 terms.
+EPS_TF32 = 2 * 2.0 ** -10 + 2.0 ** -20
 
 
 def shell_block_abs(mol, D):

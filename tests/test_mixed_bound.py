@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 from paper_2607_05622_gb300 import workloads as W
-from mixed_bound import EPS32, EPS_DIG, mixed_jk_bound
+from mixed_bound import EPS32, EPS_DIG, EPS_TF32, mixed_jk_bound
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 OUT = os.path.join(ROOT, "tests", "_build")
@@ -165,3 +165,45 @@ def test_bound_holds_for_planted_binary32_errors(oracle):
     assert np.abs(K1 - K0).max() <= bk * (1 + 1e-9)
     # and it is not vacuous: the planted change reaches a fair part of it
     assert np.abs(J1 - J0).max() >= 1e-3 * bj
+
+
+def _tf32_truncate(x):
+    """binary64 -> binary32 (round to nearest) -> TF32 by dropping the 13 low
+    significand bits (round toward zero), returned as binary64."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32)).view(np.uint32)
+    return (f & np.uint32(0xFFFFE000)).view(np.float32).astype(np.float64)
+
+
+def test_tf32_digestion_within_its_bound(oracle):
+    """The accuracy of a TF32 tensor-core digestion of the binary32 quartets,
+    emulated on the 40-AO chain of the mixed GPU test: the oracle's ERI
+    tensor, the binary32 quartets' integrals and the densities they meet
+    truncated to TF32, the sums exact.  The J and K change stays within the
+    a priori bound with EPS_TF32 (and reaches a fair part of it), and adding
+    EPS_TF32 to the mixed mode's per-quartet budget widens the mixed gate by
+    about a fifth: a TF32 digestion fits the mixed mode's error class."""
+    mol = _mixed_chain()
+    Q = oracle.schwarz(mol)
+    I = oracle.eri_tensor(mol)
+    l = np.asarray(mol.shell_l)
+    so = np.concatenate([[0], np.cumsum((l + 1) * (l + 2) // 2)])
+    sh = np.repeat(np.arange(len(l)), np.diff(so))
+    q2 = Q[sh][:, sh]
+    QQ = q2[:, :, None, None] * q2[None, None, :, :]
+    tau, tmix = 1e-12, 1e-6
+    keep = QQ >= tau
+    b32 = keep & (QQ <= tmix)
+    assert 0.01 < b32.sum() / keep.sum() < 0.5
+    D = np.random.default_rng(9).standard_normal((8, mol.nao, mol.nao))
+    J0, K0 = oracle.jk_from_tensor(np.where(keep, I, 0.0), D)
+    Ja, Ka = oracle.jk_from_tensor(np.where(keep & ~b32, I, 0.0), D)
+    Jb, Kb = oracle.jk_from_tensor(np.where(b32, _tf32_truncate(I), 0.0), _tf32_truncate(D))
+    dJ, dK = np.abs(Ja + Jb - J0).max(), np.abs(Ka + Kb - K0).max()
+    bj, bk = mixed_jk_bound(Q, mol, D, EPS_TF32, tau, tmix)
+    assert dJ <= bj and dK <= bk, (dJ, bj, dK, bk)
+    assert dJ >= 1e-3 * bj and dK >= 1e-3 * bk, (dJ, bj, dK, bk)
+    # measured: 3.8e-11 / 3.5e-11 of max|J| / max|K|
+    assert dJ < 1e-10 * np.abs(J0).max() and dK < 1e-10 * np.abs(K0).max()
+    gj, gk = mixed_jk_bound(Q, mol, D, EPS32 + EPS_DIG, tau, tmix)
+    tj, tk = mixed_jk_bound(Q, mol, D, EPS32 + EPS_DIG + EPS_TF32, tau, tmix)
+    assert tj <= 1.25 * gj and tk <= 1.25 * gk
