@@ -305,9 +305,11 @@ def _sym_terms(rng, R, N):
 
 
 def grad_workload(name, coords, kinds, seed, R, cJ=1.0, cK=0.0, tau=1e-12,
-                  symmetric=True) -> GradWorkload:
+                  symmetric=True, tz=False) -> GradWorkload:
     rng = np.random.default_rng(seed)
-    bases = draw_kind_bases(rng)
+    bases = draw_tz_bases(rng) if tz else draw_kind_bases(rng)
+    if tz:
+        kinds = tz_kinds(kinds)
     mol = build_molecule(coords, kinds, bases)
     N = mol.nao
     # same draw order as the J/K workloads up to X, so the geometry/basis agree
@@ -324,6 +326,14 @@ def config4(R: int = 16) -> GradWorkload:
     """Gradient on the 200-AO chain geometry, Gamma = sum_r P_r (x) Q_r, symmetric N(0,1)."""
     c, k = chain(10)
     return grad_workload("chain 200 AO gradient, 16 terms", c, k, seed=4, R=R, cJ=1.0, cK=0.0)
+
+
+def grad_water_tz(seed: int = 12) -> GradWorkload:
+    """Gradient on the 65-AO f-shell water (O-like 4s3p2d1f, two H 3s2p1d),
+    two non-symmetric N(0,1) terms, cJ = 1, cK = -1/2."""
+    c, k = water_like()
+    return grad_workload("water-like f-shell 65 AO gradient, 2 terms", c, k, seed=seed, R=2,
+                         cJ=1.0, cK=-0.5, tau=0.0, symmetric=False, tz=True)
 
 
 def serving_requests(n_req: int = 256, seed: int = 5, nao_lo: int = 25, nao_hi: int = 730,

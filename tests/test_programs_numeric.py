@@ -337,3 +337,72 @@ def test_f_derivative_programs_against_exact_derivatives(pe, oracle):
                       ex.ctypes.data_as(P), co.ctypes.data_as(P), out.ctypes.data_as(P), ctypes.byref(nt)) == 0
             err = np.abs(out.reshape([9] + n) - ref).max() / np.abs(ref).max()
             assert err <= tol, (cls, fn.__name__, err)
+
+
+def test_f_shell_gradient_assembled_from_the_programs(pe, oracle):
+    """The gradient of E = sum_r [cJ J(P_r,Q_r) + cK K(P_r,Q_r)] (Eq. jkderiv)
+    on the 65-AO f-shell water, assembled from the library's derivative
+    programs (the f classes built class by class as above): over canonical
+    shell quartets, each weighted by the number of distinct quartets its
+    eight-fold permutation orbit holds, its nine (centre, direction) tiles
+    contracted with Gamma averaged over the orbit, the fourth centre's
+    derivative by translational invariance.  Against the oracle's gradient
+    (tests/golden/grad_water_tz.txt, McMurchie-Davidson derivative integrals):
+    with the programs run in long double it agrees to 1e-11 of max|g|
+    (measured 2e-13), which pins the f derivative programs and the assembly
+    rule; in binary64 the deep recurrences of the f classes leave 1.0e-9,
+    within 1e-8 but above 1e-10: a gradient with f shells needs a tolerance
+    derived from binary64's rounding, not the s/p/d gradient's 1e-10."""
+    wl = W.grad_water_tz()
+    mol = wl.mol
+    g_ref = np.loadtxt(os.path.join(ROOT, "tests", "golden", "grad_water_tz.txt"))
+    G = (wl.cJ * np.einsum("rmn,rls->mnls", wl.P, wl.Q)
+         + wl.cK * np.einsum("rml,rns->mnls", wl.P, wl.Q))     # E = sum I_mnls G_mnls
+    G = G + G.transpose(1, 0, 2, 3)
+    G = G + G.transpose(0, 1, 3, 2)
+    G = (G + G.transpose(2, 3, 0, 1)) / 8                         # orbit average
+    ls = np.asarray(mol.shell_l)
+    so = np.concatenate([[0], np.cumsum((ls + 1) * (ls + 2) // 2)])
+    off = np.concatenate([[0], np.cumsum(mol.shell_nprim)])
+    cn = oracle.norm_coefs(mol)
+    Pd, Pi = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+
+    def tiles(sh, long_double):
+        L = [int(ls[s]) for s in sh]
+        n = [(l + 1) * (l + 2) // 2 for l in L]
+        ctr = np.concatenate([mol.coords[mol.shell_atom[s]] for s in sh]).astype(np.float64)
+        np_ = np.array([mol.shell_nprim[s] for s in sh], dtype=np.int32)
+        ex = np.concatenate([mol.exps[off[s]:off[s + 1]] for s in sh])
+        co = np.concatenate([cn[off[s]:off[s + 1]] for s in sh])
+        out = np.zeros(9 * int(np.prod(n)))
+        args = (ctr.ctypes.data_as(Pd), np_.ctypes.data_as(Pi), ex.ctypes.data_as(Pd),
+                co.ctypes.data_as(Pd), out.ctypes.data_as(Pd))
+        if max(L) == 3:
+            nt = ctypes.c_int(0)
+            fn = pe.pe_quartet_fderiv_ld if long_double else pe.pe_quartet_fderiv
+            assert fn(*L, *args, ctypes.byref(nt)) == 0
+        else:
+            fn = pe.pe_quartet_ld if long_double else pe.pe_quartet_d
+            assert fn(*L, 1, *args) == 0
+        return out.reshape([9] + n)
+
+    pairs = [(a, b) for a in range(len(ls)) for b in range(a + 1)]
+    err = {}
+    for long_double in (True, False):
+        g = np.zeros((mol.natoms, 3))
+        for i, (a, b) in enumerate(pairs):
+            for c, d in pairs[:i + 1]:
+                orbit = (1 + (a != b)) * (1 + (c != d)) * (1 + ((a, b) != (c, d)))
+                sh = [a, b, c, d]
+                if ls[sh[0]] < ls[sh[1]]:          # programs take l_a >= l_b, l_c >= l_d
+                    sh[0], sh[1] = sh[1], sh[0]
+                if ls[sh[2]] < ls[sh[3]]:
+                    sh[2], sh[3] = sh[3], sh[2]
+                blk = G[tuple(slice(so[s], so[s + 1]) for s in sh)]
+                v = orbit * np.einsum("tabcd,abcd->t", tiles(sh, long_double), blk).reshape(3, 3)
+                for k in range(3):
+                    g[mol.shell_atom[sh[k]]] += v[k]
+                g[mol.shell_atom[sh[3]]] -= v.sum(axis=0)
+        err[long_double] = np.abs(g - g_ref).max() / np.abs(g_ref).max()
+    assert err[True] <= 1e-11, err
+    assert 1e-10 < err[False] <= 1e-8, err

@@ -16,6 +16,9 @@ def test_configs_have_their_stated_shapes():
     wf = W.config_fshell()
     assert (wf.mol.nao, wf.ndens) == (200, 48)
     assert W.water_tz().mol.nao == 65
+    gw = W.grad_water_tz()
+    assert gw.mol.nao == 65 and gw.P.shape == (2, 65, 65) and not np.allclose(gw.P, gw.P.transpose(0, 2, 1))
+    assert max(gw.mol.shell_l) == 3 and (gw.cJ, gw.cK) == (1.0, -0.5)
 
 
 def test_draws_are_deterministic():
